@@ -1,0 +1,369 @@
+"""Benchmark: acc+jerk pair interactions per second at N = 2^20 (compensated and plain).
+
+One step = one Hermite block step of the whole hot path through the public C
+ABI (nbody_next_block -> nbody_predict -> nbody_force -> nbody_correct) on an
+equal-mass Plummer sphere of N = 2^20 particles (eps = 1e-3, Henon units).
+All particles share one power-of-two level (dt_max = dt_min = 2^-10), so every
+block holds all N particles and each step evaluates N (N - 1) pairs.
+
+Prints one JSON line.  `value` is the compensated-mode rate with inputs resident
+in device memory; `plain` holds the plain-FP32 rate; `e2e` repeats the
+compensated step with pinned host buffers (active list in, forces out);
+`roofline` relates the force kernel's own CUDA-event time to the FP32-pipe
+bound of the chip; `cpu_baseline` times the FP64 CPU oracle on a bounded
+sample of the same step.  `--impl reference` times only the oracle (the
+reference arm).  Under torchrun each rank runs an independent replica on its
+own GPU (weak scaling) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "acc+jerk pair-interactions/s at N=2^20, compensated vs plain FP32, % roofline"
+UNIT = "pair-interactions/s"
+N_DEFAULT = 1 << 20
+SEED = 3
+EPS2 = 1e-6          # eps = 1e-3
+LEVEL = 10           # shared step 2^-10: every block is all N particles
+OPS_PER_PAIR = 27    # FP32-pipe operations of one plain pair term (plus one MUFU rsqrt)
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int) -> float:
+    """Largest value over all ranks (one all-reduce); identity for one process."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, ws: int) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int) -> None:
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"nbody_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [c.strip() for c in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def make_sim(m, x, v, mode, stream):
+    from paper_astro_ph_0702058_gb300 import Simulation
+    return Simulation(m, x, v, EPS2, eta=0.02, lmin=LEVEL, lmax=LEVEL, mode=mode, stream=stream)
+
+
+def run_steps(sim, n, steps, warmup, stream, flush, host=None):
+    """Times `steps` block steps (after `warmup`).  Returns (total_ms, force_ms_list, launches)."""
+    import torch
+    dev_list = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    step_ms, force_ms = [], []
+    launches0 = 0
+    for it in range(warmup + steps):
+        if it == warmup:
+            torch.cuda.synchronize()
+            launches0 = sim.stats()["kernel_launches"]
+        flush.zero_()                     # L2 flush between steps, outside the timed events
+        e0, f0, f1, e1 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        if host is None:
+            t_blk, n_act = sim.next_block(dev_list)
+            sim.predict(t_blk)
+            f0.record(stream)
+            sim.force(dev_list, n_act)
+            f1.record(stream)
+            sim.correct(dev_list, n_act)
+        else:
+            lst, acc, jerk, pot = host
+            t_blk, n_act = sim.next_block(lst)
+            sim.predict(t_blk)
+            f0.record(stream)
+            sim.force(lst, n_act, acc=acc, jerk=jerk, pot=pot)
+            f1.record(stream)
+            sim.correct(lst, n_act)
+        e1.record(stream)
+        assert n_act == n, n_act
+        if it >= warmup:
+            step_ms.append((e0, e1))
+            force_ms.append((f0, f1))
+    sim.sync()
+    torch.cuda.synchronize()
+    launches = sim.stats()["kernel_launches"] - launches0
+    total = sum(a.elapsed_time(b) for a, b in step_ms)
+    return total, [a.elapsed_time(b) for a, b in force_ms], launches
+
+
+def roofline(force_ms_avg, n, sm_count, clocks, peaks):
+    max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    pairs = n * (n - 1)
+    achieved = pairs / (force_ms_avg * 1e-3) / 1e9
+    peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / OPS_PER_PAIR / 1e9
+    out = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Gpair/s",
+           "frac": round(achieved / peak, 4), "traffic": None,
+           "peak_basis": f"{sm_count} SM x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz / "
+                         f"{OPS_PER_PAIR} FP32 ops per pair (derived from unit counts and the max SM clock)"}
+    if clocks.get("sm_mhz"):
+        at_clock = sm_count * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / OPS_PER_PAIR / 1e9
+        out["frac_at_sampled_clock"] = round(achieved / at_clock, 4)
+    return out
+
+
+def cpu_baseline(m, x, v, n, target_s=12.0):
+    """FP64 oracle, one step of the same workload on a bounded sample of active rows."""
+    import numpy as np
+
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    st = oracle.State(m, x, v, EPS2, 0.02, lmin=LEVEL, lmax=LEVEL)
+    st.level[:] = LEVEL
+    t_new = 1
+    xp, vp = st.predict(t_new)        # predictor over all N (part of the sample's cost)
+    rows = 64
+    t0 = time.perf_counter()
+    act = np.arange(rows, dtype=np.int32)
+    fa, fk, _ = oracle.force(m, xp, vp, EPS2, act)
+    dt = time.perf_counter() - t0
+    rows = int(min(n, max(rows, rows * target_s / max(dt, 1e-3))))
+    act = np.linspace(0, n - 1, rows).astype(np.int32)
+    t0 = time.perf_counter()
+    xp, vp = st.predict(t_new)
+    fa, fk, _ = oracle.force(m, xp, vp, EPS2, act)
+    st.correct(act, xp, vp, fa, fk, t_new)
+    dt = time.perf_counter() - t0
+    return {"value": rows * (n - 1) / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"one step (predict all {n}, force on {rows} evenly spaced rows against all {n}, "
+                      f"correct those rows) in FP64, {dt:.1f} s"}
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+
+    from synthetic import plummer_sphere
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    n = args.n
+    m, x, v = plummer_sphere(n, SEED + rank)  # independent replica per rank
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = measured_peaks()
+    res = {}
+    with torch.cuda.stream(stream):
+        for mode in ("comp", "plain"):
+            sim = make_sim(m, x, v, mode, stream)
+            barrier(ws)
+            with ClockSampler(local) as cs:
+                t0 = time.perf_counter()
+                total_ms, force_ms, launches = run_steps(sim, n, args.steps, args.warmup, stream, flush)
+                wall = time.perf_counter() - t0
+            clocks = cs.summary()
+            cfg = sim.stats()
+            sim.close()
+            t_max = max_over_ranks(total_ms, ws)
+            pairs_all = sum_over_ranks(args.steps * n * (n - 1), ws)
+            res[mode] = {"value": pairs_all / (t_max * 1e-3), "ms_per_step": t_max / args.steps,
+                         "force_ms": statistics.mean(force_ms), "launches": launches, "clocks": clocks,
+                         "wall_s": wall, "shape": f"{cfg['last_threads']} threads x {cfg['last_i_per_thread']} "
+                                                  f"i/thread, j-split {cfg['last_j_split']}"}
+        # end to end: pinned host list in/out and forces back to the host every step
+        sim = make_sim(m, x, v, "comp", stream)
+        host = (torch.zeros(n, dtype=torch.int32).pin_memory(), torch.zeros((n, 3), dtype=torch.float64).pin_memory(),
+                torch.zeros((n, 3), dtype=torch.float64).pin_memory(), torch.zeros(n, dtype=torch.float64).pin_memory())
+        barrier(ws)
+        e2e_ms, _, _ = run_steps(sim, n, args.steps, args.warmup, stream, flush, host=host)
+        sim.close()
+        e2e_max = max_over_ranks(e2e_ms, ws)
+    out = None
+    if rank == 0:
+        c = res["comp"]
+        p = res["plain"]
+        rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks)
+        rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks)
+        out = {
+            "metric": METRIC, "value": c["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": c["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "precision": "compensated: FP32 pair math on hi/lo splits of FP64 positions, double-single sums; "
+                         "FP64 predictor, corrector, time bins and state",
+            "data": "synthetic (seeded Plummer sphere, Henon units)",
+            "config": {"workload": f"Plummer N={n} eps=1e-3, full-force Hermite block step (all N active, "
+                                   f"shared level dt=2^-{LEVEL}): schedule+predict+force+correct",
+                       "n": n, "n_act": n, "pairs_per_step": n * (n - 1), "l2": "flushed between steps "
+                       f"({L2_FLUSH_BYTES >> 20} MiB write, outside the timed events)",
+                       "force_launch_shape": c["shape"], "parallelism": f"replicas x{ws}"},
+            "roofline": rl_c,
+            "plain": {"value": p["value"], "ms_per_step": p["ms_per_step"], "roofline": rl_p,
+                      "force_launch_shape": p["shape"], "clocks": p["clocks"]},
+            "comp_over_plain": c["value"] / p["value"],
+            "e2e": {"value": sum_over_ranks(args.steps * n * (n - 1), ws) / (e2e_max * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * 4 * n, "d2h_bytes_per_step": 4 * n + 7 * 8 * n},
+            "gpu_launches": c["launches"],
+            "clocks": c["clocks"],
+            "context": {"paper_8800GTX_pairs_per_s": 1.23e9, "paper_GRAPE6Af_pairs_per_s": 2.16e9,
+                        "note": "Table 4 per-interaction times of the paper, other hardware; not a target"},
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(m, x, v, n)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def bench_reference(args):
+    """The reference arm: the FP64 oracle, timed on the host cores, same workload and metric."""
+    import numpy as np
+
+    import oracle
+    from synthetic import plummer_sphere
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    n = args.n
+    m, x, v = plummer_sphere(n, SEED)
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    st = oracle.State(m, x, v, EPS2, 0.02, lmin=LEVEL, lmax=LEVEL)
+    st.level[:] = LEVEL
+    per_step_s = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    rows = 16
+    times = []
+    for it in range(args.warmup + args.steps):
+        act = np.linspace(0, n - 1, rows).astype(np.int32)
+        t0 = time.perf_counter()
+        xp, vp = st.predict(int(st.t.max()) + 1)
+        fa, fk, _ = oracle.force(m, xp, vp, EPS2, act)
+        st.correct(act, xp, vp, fa, fk, int(st.t.max()) + 1)
+        st.level[:] = LEVEL
+        st.t[:] = st.t.max()
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append((rows, dt))
+        rows = int(min(n, max(16, rows * per_step_s / max(dt, 1e-3))))
+    pairs = sum(r * (n - 1) for r, _ in times)
+    secs = sum(t for _, t in times)
+    value = pairs / secs
+    sample = (f"each step: predict all {n}, force on a bounded sample of evenly spaced rows "
+              f"(~{per_step_s:.0f} s of CPU work) against all {n}, correct those rows; FP64")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Plummer sphere, Henon units)",
+            "config": {"workload": f"Plummer N={n} eps=1e-3, full-force Hermite block step (all N active, "
+                                   f"shared level dt=2^-{LEVEL}): schedule+predict+force+correct", "n": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="particles (default 2^20)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    out = bench_reference(args) if args.impl == "reference" else bench_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

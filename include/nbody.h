@@ -1,0 +1,225 @@
+/*
+ * nbody.h -- C ABI of libnbody.so, a GB300 (sm_103a) implementation of the
+ * direct-summation force evaluation inside the 4th-order Hermite
+ * predictor-corrector with power-of-two block time steps of Portegies Zwart,
+ * Belleman & Geldof (2007), "High Performance Direct Gravitational N-body
+ * Simulations on Graphics Processing Units".
+ *
+ * The calls follow the paper's statement of one integration step (Sect. 2,
+ * the bulleted step list): choose the block of particles with the smallest
+ * t_i + dt_i (nbody_next_block), predict every particle to the block time
+ * (nbody_predict), recompute acceleration, jerk and potential of the block
+ * (nbody_force), and correct the block to fourth order with new time steps
+ * (nbody_correct).
+ *
+ * Conventions used by every call:
+ *   - Units: G = 1.  eps2 is the square of the Plummer softening length
+ *     (Appendix A: r^2 = eps^2 + |x_j - x_i|^2).
+ *   - Vectors exchanged with the caller are n x 3 row-major arrays of double
+ *     (x0 y0 z0 x1 y1 z1 ...).  Index lists are int32, 0 <= i < n.
+ *   - Time steps are powers of two, dt = 2^-level with
+ *     lmin <= level <= lmax (dt_max = 2^-lmin, dt_min = 2^-lmax; the paper
+ *     uses dt_min = 2^-26).  Time is counted internally in int64 ticks of
+ *     dt_min; a time passed in as a double must be a whole number of ticks.
+ *   - Pointers: every pointer argument may point to host memory or to device
+ *     memory of the context's device (detected with cudaPointerGetAttributes),
+ *     unless stated otherwise.  The caller keeps ownership of all its
+ *     buffers; the library copies inputs, writes outputs, and holds no caller
+ *     pointer after a call returns.
+ *   - Streams: all device work of a context runs on the stream given in
+ *     nbody_params.stream (NULL: the legacy default stream).  A call that
+ *     returns data in host memory synchronises that stream before it returns;
+ *     a call whose outputs are device memory or NULL returns without waiting.
+ *   - Errors: every int-returning call returns NBODY_OK (0) or a negative
+ *     NBODY_E* code and never aborts the process.  nbody_strerror() gives a
+ *     static description of a code; nbody_last_error() the detailed message
+ *     of the most recent failure in the calling thread.
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBODY_ABI_VERSION 1
+
+enum {
+    NBODY_OK = 0,
+    NBODY_EINVAL = -1,     /* bad argument (null where required, out of range, bad time) */
+    NBODY_ENOMEM = -2,     /* device or pinned-host allocation failed                       */
+    NBODY_ECUDA = -3,      /* a CUDA runtime call failed (message in nbody_last_error)       */
+    NBODY_EDTMIN = -4,     /* strict mode: a criterion asked for dt < dt_min                  */
+    NBODY_ENONFINITE = -5, /* a corrected state or force was NaN or infinite                  */
+    NBODY_ENOTSYNC = -6,   /* energy requested while particles sit at different times         */
+    NBODY_ETIMEOUT = -7,   /* a bounded device-side wait gave up (error flag, no hang)       */
+    NBODY_ESTATE = -8      /* call out of order (e.g. correct without a matching force)      */
+};
+
+/* Force-evaluation precision (the pair loop; FP64 everywhere else). */
+enum {
+    NBODY_MODE_PLAIN = 0,  /* FP32 pair math on FP32 positions, FP32 accumulation           */
+    NBODY_MODE_COMP = 1    /* FP32 pair math on x_j - x_i formed from hi/lo splits of the
+                              FP64 positions; double-single (compensated) accumulation      */
+};
+
+typedef struct nbody_ctx nbody_ctx; /* opaque; owns all of its device memory */
+
+typedef struct {
+    double eta;       /* accuracy parameter nu of Eq. (timestep); the paper uses 0.01     */
+    double eta_init;  /* nu of Eq. (initTimestep); <= 0 means "same as eta"               */
+    int lmin;         /* dt_max = 2^-lmin (paper: 0.125, lmin = 3)                          */
+    int lmax;         /* dt_min = 2^-lmax (paper: 2^-26, lmax = 26); 0 <= lmin <= lmax <= 40 */
+    int mode;         /* NBODY_MODE_PLAIN or NBODY_MODE_COMP                                 */
+    int strict;       /* nonzero: a step clamped at dt_min makes nbody_correct fail with
+                         NBODY_EDTMIN (the step is still taken); zero: it is only counted */
+    int i_block;      /* force tuning, 0 = automatic: i-particles per thread (1, 2 or 4)    */
+    int j_tile;       /* force tuning, 0 = automatic: threads per block (64, 128 or 256)    */
+    int j_split;      /* force tuning, 0 = automatic: number of j-ranges (>= 1)             */
+    void *stream;     /* cudaStream_t for all work of the context, or NULL                  */
+} nbody_params;
+
+/* Fills *p with the defaults: eta 0.01, eta_init = eta, lmin 6, lmax 26, plain
+ * mode, not strict, automatic tuning, NULL stream. */
+void nbody_default_params(nbody_params *p);
+
+/* Start of a run (Sect. 2; initial time step Eq. initTimestep).
+ * Creates a context on the current CUDA device for n >= 1 particles:
+ * m[n] masses, x[n*3] positions, v[n*3] velocities (copied; host or device),
+ * softening eps2 >= 0.  Computes the full force on all particles at t = 0
+ * and each particle's first level from dt = eta_init |a| / |k|.
+ * On success *out receives the context (free with nbody_free).
+ * Errors: EINVAL (null pointer, n < 1 or n > 2^31 - 1, eps2 < 0, bad levels or
+ * mode), ENOMEM, ECUDA, ENONFINITE (non-finite input or initial force). */
+int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x,
+               const double *v, double eps2, const nbody_params *p);
+
+/* Block scheduler (Sect. 2, first bullet): t_blk = min_i (t_i + dt_i); the
+ * block is every i with t_i + dt_i == t_blk exactly, in ascending index.
+ * Writes the block time (double) to *t_blk, its size to *n_act, and the list
+ * to active[0 .. n_act) when active is not NULL (room for n entries needed).
+ * Synchronises the context stream.  Errors: EINVAL (null t_blk / n_act). */
+int nbody_next_block(nbody_ctx *ctx, double *t_blk, int64_t *n_act, int32_t *active);
+
+/* Predictor (Sect. 2): x_p = x + v dt + a dt^2/2 + k dt^3/6 and
+ * v_p = v + a dt + k dt^2/2 for ALL particles, dt = t - t_i, in FP64; stores
+ * the predicted positions/velocities as the FP32 j-stream that nbody_force
+ * reads.  t must be a whole number of ticks and >= every t_i.
+ * Errors: EINVAL (t not on the tick grid or before some t_i). */
+int nbody_predict(nbody_ctx *ctx, double t);
+
+/* Force on the listed particles from all n predicted particles (Eq. Force with
+ * the softened pair term of Appendix A; j = i excluded):
+ *   a_i   = sum_j m_j dx / r^3
+ *   k_i   = sum_j m_j (dv / r^3 - 3 (dx.dv) dx / r^5)
+ *   phi_i = -sum_j m_j / r,    dx = x_j - x_i, dv = v_j - v_i, r^2 = eps2 + dx.dx
+ * evaluated at the state of the last nbody_predict.  active[n_act] (host or
+ * device) lists distinct or repeated indices; 0 <= n_act <= n.  Results for
+ * row q (particle active[q]) go to acc[q*3..], jerk[q*3..], pot[q] when those
+ * pointers are not NULL (host or device, double); they are always kept in the
+ * context for nbody_correct.  Errors: EINVAL (index out of range is checked on
+ * the device and reported here when outputs are host memory, else at the next
+ * synchronising call), ESTATE (no prediction yet), ETIMEOUT. */
+int nbody_force(nbody_ctx *ctx, const int32_t *active, int64_t n_act,
+                double *acc, double *jerk, double *pot);
+
+/* Corrector of Sect. 2 and the new time step of Eq. (timestep) for the listed
+ * particles, which must be distinct.  Row q of the forces belongs to
+ * active[q].  acc/jerk (n_act x 3, host or device) supply the forces at the
+ * predicted state; both NULL means "the results of the last nbody_force",
+ * which must then have had the same n_act.  The corrected step ends at the
+ * time of the last nbody_predict.  New level: largest power of two <= the
+ * criterion, clamped to [dt_min, dt_max]; it shrinks at once and grows by
+ * one level at most, only when the new time is a multiple of twice the old
+ * step.  Errors: EINVAL, ESTATE, ENONFINITE (state updated; flagged rows are
+ * set to dt_min), EDTMIN (strict mode only). */
+int nbody_correct(nbody_ctx *ctx, const int32_t *active, int64_t n_act,
+                  const double *acc, const double *jerk);
+
+/* Block steps (schedule -> predict -> force -> correct) until every particle
+ * has reached t_end (a multiple of dt_max, >= the current time), or until
+ * max_steps blocks have been taken (max_steps <= 0: no limit).  *n_steps
+ * (may be NULL) receives the number of blocks taken.  Errors: as the calls
+ * it makes; EINVAL when t_end is not a multiple of dt_max. */
+int nbody_step(nbody_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps);
+
+/* Energy diagnostic at a synchronised time (every t_i equal):
+ * E_kin = sum m v^2 / 2, E_pot = sum_i m_i phi_i / 2 with the softened phi_i
+ * (j = i excluded), in FP64 on the device.  Synchronises the stream.
+ * Errors: ENOTSYNC when the particles are not at one time. */
+int nbody_energy(nbody_ctx *ctx, double *ekin, double *epot);
+
+/* Waits for all work of the context and reports device-side errors raised
+ * since the last report: ETIMEOUT (a bounded wait gave up), EINVAL (an index
+ * out of range in an active list), ENONFINITE (a non-finite corrected row),
+ * EDTMIN (strict mode: a step clamped at dt_min).  Calls that synchronise
+ * (nbody_next_block, nbody_energy, nbody_get_state, nbody_step, and
+ * nbody_force with host outputs) report the same errors. */
+int nbody_sync(nbody_ctx *ctx);
+
+/* Checkpoint: copies the FP64 state into caller buffers (host or device;
+ * any may be NULL): x, v, a, k (n x 3), t_tick (n, ticks of dt_min) and
+ * level (n).  Synchronises the stream. */
+int nbody_get_state(nbody_ctx *ctx, double *x, double *v, double *a, double *k,
+                    int64_t *t_tick, int8_t *level);
+
+/* Resume: overwrites the whole state from caller buffers (none may be NULL;
+ * masses and eps2 stay those of nbody_init).  Requires every t_tick to be a
+ * multiple of its step 2^(lmax - level) and lmin <= level <= lmax.
+ * Invalidates the last prediction and force.  Errors: EINVAL. */
+int nbody_set_state(nbody_ctx *ctx, const double *x, const double *v, const double *a,
+                    const double *k, const int64_t *t_tick, const int8_t *level);
+
+/* Copies the predicted j-stream of the last nbody_predict into caller
+ * buffers (host or device; any may be NULL), n x 4 floats each:
+ * posm = (x_hi, y_hi, z_hi, m), vel = (vx, vy, vz, 0) and, in compensated
+ * mode, poslo = (x - x_hi, y - y_hi, z - z_hi, 0) rounded to float (zeros in
+ * plain mode).  Synchronises the stream.  Errors: ESTATE (no prediction). */
+int nbody_get_predicted(nbody_ctx *ctx, float *posm, float *vel, float *poslo);
+
+/* Counters of the context since nbody_init. */
+typedef struct {
+    int64_t n;             /* particles                                            */
+    int64_t n_pad;         /* j-stream length (n rounded up to the tile length)    */
+    int64_t blocks;        /* block steps corrected                                */
+    int64_t below_dt_min;  /* steps clamped at dt_min                              */
+    int64_t nonfinite;     /* corrected rows found non-finite                      */
+    int64_t force_calls;   /* nbody_force calls                                    */
+    int64_t pairs;         /* pair interactions evaluated: sum of n_act * (n - 1)  */
+    int64_t kernel_launches; /* device kernels launched by the library            */
+    int last_threads;      /* launch shape of the last force kernel               */
+    int last_i_per_thread;
+    int last_j_split;
+    int mode;
+} nbody_stats;
+
+int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);
+
+/* Releases every resource of the context (NULL is allowed). */
+void nbody_free(nbody_ctx *ctx);
+
+/* Static description of an NBODY_* code. */
+const char *nbody_strerror(int code);
+
+/* Detailed message of the last failure in this thread ("" if none). */
+const char *nbody_last_error(void);
+
+/* Test hook: the k-th device allocation from now fails with ENOMEM
+ * (k >= 1; 0 disables).  Lets the out-of-memory paths be exercised. */
+void nbody_debug_fail_alloc(int k);
+
+/* Test hook: while on (nonzero), force kernels launched from this process do
+ * not issue the copy of their first j-tile, so each block's bounded wait for
+ * that tile gives up after about 2 s; the kernel records the timeout and
+ * returns, and the call reports NBODY_ETIMEOUT.  Nothing faults or hangs and
+ * the context stays usable.  Exercises the failure path of the device waits. */
+void nbody_debug_skip_tile_copy(int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

@@ -1,0 +1,104 @@
+"""GB300 (sm_103a) direct N-body force evaluation for the 4th-order Hermite
+block-time-step integrator of Portegies Zwart, Belleman & Geldof (2007).
+
+The work is done by ``libnbody.so`` (CUDA kernels behind the C ABI of
+``include/nbody.h``).  ``_lib`` mirrors the C calls one to one; ``Simulation``
+below only owns a context handle and forwards to them.  PyTorch is used only
+by callers, for device memory and streams.
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBodyError,  # noqa: F401
+                   nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_default_params, nbody_energy,
+                   nbody_force, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
+                   nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
+                   nbody_strerror, nbody_sync)
+
+MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP}
+
+
+class Simulation:
+    """One library context: masses, FP64 state and j-stream on the current CUDA device.
+
+    ``m`` (n,), ``x`` and ``v`` (n, 3) float64, numpy or torch (host or CUDA).
+    ``stream``: a ``torch.cuda.Stream`` (or raw ``cudaStream_t`` int); None
+    selects the legacy default stream.
+    """
+
+    def __init__(self, m, x, v, eps2, *, eta=0.01, eta_init=None, lmin=6, lmax=26, mode="plain",
+                 strict=False, i_block=0, j_tile=0, j_split=0, stream=None):
+        p = nbody_default_params()
+        p.eta = float(eta)
+        p.eta_init = float(eta_init) if eta_init is not None else 0.0
+        p.lmin, p.lmax = int(lmin), int(lmax)
+        p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        p.strict = 1 if strict else 0
+        p.i_block, p.j_tile, p.j_split = int(i_block), int(j_tile), int(j_split)
+        if stream is not None:
+            p.stream = int(getattr(stream, "cuda_stream", stream))
+        self.n = int(m.shape[0])
+        self.lmin, self.lmax = p.lmin, p.lmax
+        self.mode = p.mode
+        self.stream = stream
+        self._ctx = nbody_init(self.n, m, x, v, eps2, p)
+
+    @property
+    def handle(self):
+        if self._ctx is None:
+            raise RuntimeError("simulation closed")
+        return self._ctx
+
+    def next_block(self, active=None):
+        """(t_blk, n_act); the block's indices go to ``active`` (int32, room for n) if given."""
+        return nbody_next_block(self.handle, active)
+
+    def predict(self, t):
+        nbody_predict(self.handle, t)
+
+    def force(self, active, n_act=None, acc=None, jerk=None, pot=None):
+        n_act = int(active.shape[0]) if n_act is None else int(n_act)
+        nbody_force(self.handle, active, n_act, acc, jerk, pot)
+
+    def correct(self, active, n_act=None, acc=None, jerk=None):
+        n_act = int(active.shape[0]) if n_act is None else int(n_act)
+        nbody_correct(self.handle, active, n_act, acc, jerk)
+
+    def step(self, t_end, max_steps=0):
+        return nbody_step(self.handle, t_end, max_steps)
+
+    def sync(self):
+        nbody_sync(self.handle)
+
+    def energy(self):
+        return nbody_energy(self.handle)
+
+    def get_state(self, x=None, v=None, a=None, k=None, t_tick=None, level=None):
+        nbody_get_state(self.handle, self.n, x, v, a, k, t_tick, level)
+
+    def set_state(self, x, v, a, k, t_tick, level):
+        nbody_set_state(self.handle, self.n, x, v, a, k, t_tick, level)
+
+    def get_predicted(self, posm=None, vel=None, poslo=None):
+        nbody_get_predicted(self.handle, self.n, posm, vel, poslo)
+
+    def stats(self):
+        s = nbody_get_stats(self.handle)
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if self._ctx is not None:
+            nbody_free(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

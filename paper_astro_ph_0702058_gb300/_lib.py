@@ -1,0 +1,246 @@
+"""ctypes binding of libnbody.so (argument marshalling only).
+
+Every function here has the name and arguments of the C call in
+``include/nbody.h`` and does nothing but convert Python objects to pointers
+and sizes and turn a negative return code into ``NBodyError``.  All work
+runs in the library's CUDA kernels; there is no CPU fallback: if the library
+is missing or cannot be loaded, every call raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); they must be C-contiguous with the dtype the C call expects.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from .build import LIB
+
+_lock = threading.Lock()
+_lib = None
+
+NBODY_OK = 0
+NBODY_EINVAL = -1
+NBODY_ENOMEM = -2
+NBODY_ECUDA = -3
+NBODY_EDTMIN = -4
+NBODY_ENONFINITE = -5
+NBODY_ENOTSYNC = -6
+NBODY_ETIMEOUT = -7
+NBODY_ESTATE = -8
+NBODY_MODE_PLAIN = 0
+NBODY_MODE_COMP = 1
+
+# Every symbol include/nbody.h declares (checked by the tests against the header).
+EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",
+           "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state",
+           "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
+           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy")
+
+
+class nbody_params(C.Structure):
+    _fields_ = [("eta", C.c_double), ("eta_init", C.c_double), ("lmin", C.c_int), ("lmax", C.c_int),
+                ("mode", C.c_int), ("strict", C.c_int), ("i_block", C.c_int), ("j_tile", C.c_int),
+                ("j_split", C.c_int), ("stream", C.c_void_p)]
+
+
+class nbody_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_pad", C.c_int64), ("blocks", C.c_int64), ("below_dt_min", C.c_int64),
+                ("nonfinite", C.c_int64), ("force_calls", C.c_int64), ("pairs", C.c_int64),
+                ("kernel_launches", C.c_int64), ("last_threads", C.c_int), ("last_i_per_thread", C.c_int),
+                ("last_j_split", C.c_int), ("mode", C.c_int)]
+
+
+class NBodyError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        self.code = code
+        super().__init__(f"{where}: {detail} (code {code})")
+
+
+def lib_path() -> str:
+    return os.environ.get("NBODY_LIB", LIB)
+
+
+def lib():
+    """Loads libnbody.so (raises if it has not been built: no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libnbody.so not built ({path}); run __graft_entry__.build()")
+            L = C.CDLL(path)
+            P = C.c_void_p
+            L.nbody_default_params.argtypes = [C.POINTER(nbody_params)]
+            L.nbody_default_params.restype = None
+            L.nbody_init.argtypes = [C.POINTER(C.c_void_p), C.c_int64, P, P, P, C.c_double, C.POINTER(nbody_params)]
+            L.nbody_next_block.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), P]
+            L.nbody_predict.argtypes = [P, C.c_double]
+            L.nbody_force.argtypes = [P, P, C.c_int64, P, P, P]
+            L.nbody_correct.argtypes = [P, P, C.c_int64, P, P]
+            L.nbody_step.argtypes = [P, C.c_double, C.c_int64, C.POINTER(C.c_int64)]
+            L.nbody_sync.argtypes = [P]
+            L.nbody_energy.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.nbody_get_state.argtypes = [P, P, P, P, P, P, P]
+            L.nbody_set_state.argtypes = [P, P, P, P, P, P, P]
+            L.nbody_get_predicted.argtypes = [P, P, P, P]
+            L.nbody_get_stats.argtypes = [P, C.POINTER(nbody_stats)]
+            L.nbody_free.argtypes = [P]
+            L.nbody_free.restype = None
+            L.nbody_strerror.argtypes = [C.c_int]
+            L.nbody_strerror.restype = C.c_char_p
+            L.nbody_last_error.argtypes = []
+            L.nbody_last_error.restype = C.c_char_p
+            L.nbody_debug_fail_alloc.argtypes = [C.c_int]
+            L.nbody_debug_fail_alloc.restype = None
+            L.nbody_debug_skip_tile_copy.argtypes = [C.c_int]
+            L.nbody_debug_skip_tile_copy.restype = None
+            for name in ("nbody_init", "nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct",
+                         "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state", "nbody_set_state",
+                         "nbody_get_predicted", "nbody_get_stats"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != NBODY_OK:
+        detail = lib().nbody_last_error().decode() or lib().nbody_strerror(code).decode()
+        raise NBodyError(code, where, detail)
+
+
+_DTYPES = {"f64": ("float64", "torch.float64"), "i32": ("int32", "torch.int32"),
+           "i64": ("int64", "torch.int64"), "i8": ("int8", "torch.int8")}
+
+
+def ptr(a, kind: str, min_len: int = 0):
+    """Raw address of a contiguous numpy array / torch tensor of dtype ``kind`` (None passes NULL)."""
+    if a is None:
+        return None
+    np_name, torch_name = _DTYPES[kind]
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        if str(a.dtype) != torch_name:
+            raise TypeError(f"expected {torch_name}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if a.numel() < min_len:
+            raise ValueError(f"buffer holds {a.numel()} elements, need {min_len}")
+        return C.c_void_p(a.data_ptr())
+    if hasattr(a, "__array_interface__"):
+        if str(a.dtype) != np_name:
+            raise TypeError(f"expected {np_name}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.size < min_len:
+            raise ValueError(f"buffer holds {a.size} elements, need {min_len}")
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def nbody_default_params() -> nbody_params:
+    p = nbody_params()
+    lib().nbody_default_params(C.byref(p))
+    return p
+
+
+def nbody_init(n: int, m, x, v, eps2: float, params: nbody_params):
+    h = C.c_void_p()
+    _check(lib().nbody_init(C.byref(h), int(n), ptr(m, "f64", n), ptr(x, "f64", 3 * n), ptr(v, "f64", 3 * n),
+                            float(eps2), C.byref(params)), "nbody_init")
+    return h
+
+
+def nbody_next_block(ctx, active=None):
+    t = C.c_double()
+    na = C.c_int64()
+    _check(lib().nbody_next_block(ctx, C.byref(t), C.byref(na), ptr(active, "i32")), "nbody_next_block")
+    return t.value, na.value
+
+
+def nbody_predict(ctx, t: float) -> None:
+    _check(lib().nbody_predict(ctx, float(t)), "nbody_predict")
+
+
+def nbody_force(ctx, active, n_act: int, acc=None, jerk=None, pot=None) -> None:
+    _check(lib().nbody_force(ctx, ptr(active, "i32", n_act), int(n_act), ptr(acc, "f64", 3 * n_act),
+                             ptr(jerk, "f64", 3 * n_act), ptr(pot, "f64", n_act)), "nbody_force")
+
+
+def nbody_correct(ctx, active, n_act: int, acc=None, jerk=None) -> None:
+    _check(lib().nbody_correct(ctx, ptr(active, "i32", n_act), int(n_act), ptr(acc, "f64", 3 * n_act),
+                               ptr(jerk, "f64", 3 * n_act)), "nbody_correct")
+
+
+def nbody_step(ctx, t_end: float, max_steps: int = 0) -> int:
+    ns = C.c_int64()
+    _check(lib().nbody_step(ctx, float(t_end), int(max_steps), C.byref(ns)), "nbody_step")
+    return ns.value
+
+
+def nbody_sync(ctx) -> None:
+    _check(lib().nbody_sync(ctx), "nbody_sync")
+
+
+def nbody_energy(ctx):
+    ek, ep = C.c_double(), C.c_double()
+    _check(lib().nbody_energy(ctx, C.byref(ek), C.byref(ep)), "nbody_energy")
+    return ek.value, ep.value
+
+
+def nbody_get_state(ctx, n, x=None, v=None, a=None, k=None, t_tick=None, level=None) -> None:
+    _check(lib().nbody_get_state(ctx, ptr(x, "f64", 3 * n), ptr(v, "f64", 3 * n), ptr(a, "f64", 3 * n),
+                                 ptr(k, "f64", 3 * n), ptr(t_tick, "i64", n), ptr(level, "i8", n)),
+           "nbody_get_state")
+
+
+def nbody_set_state(ctx, n, x, v, a, k, t_tick, level) -> None:
+    _check(lib().nbody_set_state(ctx, ptr(x, "f64", 3 * n), ptr(v, "f64", 3 * n), ptr(a, "f64", 3 * n),
+                                 ptr(k, "f64", 3 * n), ptr(t_tick, "i64", n), ptr(level, "i8", n)),
+           "nbody_set_state")
+
+
+_F32 = ("float32", "torch.float32")
+
+
+def _ptr_f32(a, min_len):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != _F32[1] or not a.is_contiguous() or a.numel() < min_len:
+            raise ValueError("need a contiguous float32 tensor of n x 4")
+        return C.c_void_p(a.data_ptr())
+    if str(a.dtype) != _F32[0] or not a.flags["C_CONTIGUOUS"] or a.size < min_len:
+        raise ValueError("need a C-contiguous float32 array of n x 4")
+    return C.c_void_p(a.ctypes.data)
+
+
+def nbody_get_predicted(ctx, n, posm=None, vel=None, poslo=None) -> None:
+    _check(lib().nbody_get_predicted(ctx, _ptr_f32(posm, 4 * n), _ptr_f32(vel, 4 * n), _ptr_f32(poslo, 4 * n)),
+           "nbody_get_predicted")
+
+
+def nbody_get_stats(ctx) -> nbody_stats:
+    s = nbody_stats()
+    _check(lib().nbody_get_stats(ctx, C.byref(s)), "nbody_get_stats")
+    return s
+
+
+def nbody_free(ctx) -> None:
+    lib().nbody_free(ctx)
+
+
+def nbody_strerror(code: int) -> str:
+    return lib().nbody_strerror(int(code)).decode()
+
+
+def nbody_last_error() -> str:
+    return lib().nbody_last_error().decode()
+
+
+def nbody_debug_fail_alloc(k: int) -> None:
+    lib().nbody_debug_fail_alloc(int(k))
+
+
+def nbody_debug_skip_tile_copy(on: bool) -> None:
+    lib().nbody_debug_skip_tile_copy(1 if on else 0)

@@ -1,0 +1,635 @@
+// Host side of the C ABI declared in include/nbody.h: context ownership,
+// argument checks, host/device pointer handling, the block-step call
+// sequence of Sect. 2 of Portegies Zwart, Belleman & Geldof (2007), and
+// reporting of device-side status flags.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nbody_internal.cuh"
+
+using namespace nb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+int g_fail_alloc = 0;  // allocation-failure injection countdown (test hook)
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear a sticky launch error of this thread
+    return fail(e == cudaErrorMemoryAllocation ? NBODY_ENOMEM : NBODY_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define NB_CUDA(call, what)                         \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes ? bytes : 16);
+}
+
+cudaError_t host_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (g_fail_alloc > 0 && --g_fail_alloc == 0) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes ? bytes : 16);
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct nbody_ctx {
+    int64_t n = 0, n_pad = 0;
+    double eps2 = 0.0;
+    nbody_params p{};
+    cudaStream_t s = nullptr;
+    int sm_count = 0;
+
+    double *state = nullptr;  // 13 n doubles: m, x[3], v[3], a[3], k[3]
+    int64_t *t = nullptr;
+    int8_t *level = nullptr;
+    float4 *jbuf = nullptr;   // 3 n_pad float4: posm, vel, poslo
+    int32_t *act_force = nullptr, *act_corr = nullptr, *act_sched = nullptr;
+    double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
+    double *stage = nullptr;  // 6 n doubles: external forces / AoS staging
+    void *partials = nullptr;
+    size_t partials_cap = 0;
+    void *sched_scratch = nullptr;
+    SchedOut *sched_out = nullptr;
+    DevStatus *st = nullptr;
+    double *phi = nullptr;
+    double *e_out = nullptr;
+    unsigned long long *trange = nullptr;
+    // pinned host mirrors
+    SchedOut *sched_host = nullptr;
+    DevStatus *st_host = nullptr;
+    double *e_host = nullptr;
+    unsigned long long *trange_host = nullptr;
+
+    State S{};
+    JStream J{};
+    int64_t t_max = 0;      // largest t_i (ticks)
+    int64_t t_pred = 0;     // time of the last prediction (ticks)
+    bool pred_valid = false;
+    int64_t force_n_act = -1;
+    nbody_stats stats{};
+};
+
+namespace {
+
+void release(nbody_ctx *c)
+{
+    void *dev[] = {c->state, c->t, c->level, c->jbuf, c->act_force, c->act_corr, c->act_sched,
+                   c->f_acc, c->f_jerk, c->f_pot, c->stage, c->partials, c->sched_scratch,
+                   c->sched_out, c->st, c->phi, c->e_out, c->trange};
+    for (void *d : dev)
+        if (d) cudaFree(d);
+    void *host[] = {c->sched_host, c->st_host, c->e_host, c->trange_host};
+    for (void *h : host)
+        if (h) cudaFreeHost(h);
+    delete c;
+}
+
+int to_ticks(const nbody_ctx *c, double t, int64_t *out)
+{
+    const double tt = std::ldexp(t, c->p.lmax);
+    if (!std::isfinite(tt) || tt < 0.0 || tt > 4.0e18 || tt != std::floor(tt))
+        return fail(NBODY_EINVAL, "time %.17g is not a non-negative multiple of dt_min = 2^-%d", t, c->p.lmax);
+    *out = static_cast<int64_t>(tt);
+    return NBODY_OK;
+}
+
+// Copies n bytes from a host or device pointer into device memory.
+cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+}
+
+// Reads the device status after the stream has drained and turns raised flags
+// into an error code (the flags are then cleared; the counters keep counting).
+int absorb_status(nbody_ctx *c)
+{
+    const DevStatus h = *c->st_host;
+    c->stats.below_dt_min = static_cast<int64_t>(h.below_min);
+    c->stats.nonfinite = static_cast<int64_t>(h.nonfinite);
+    const unsigned f = h.flags;
+    if (!f) return NBODY_OK;
+    cudaMemsetAsync(&c->st->flags, 0, sizeof(unsigned), c->s);
+    c->st_host->flags = 0;
+    if (f & kFlagTimeout) return fail(NBODY_ETIMEOUT, "a device-side wait for a j-tile gave up (bounded wait)");
+    if (f & kFlagBadIndex)
+        return fail(NBODY_EINVAL, "active list row %d holds an index outside [0, %lld)", h.bad_index,
+                    static_cast<long long>(c->n));
+    if (f & kFlagNonfinite)
+        return fail(NBODY_ENONFINITE, "non-finite force or corrected state (%llu rows so far)", h.nonfinite);
+    if ((f & kFlagDtMin) && c->p.strict)
+        return fail(NBODY_EDTMIN, "a time-step criterion fell below dt_min = 2^-%d (%llu clamps so far)",
+                    c->p.lmax, h.below_min);
+    return NBODY_OK;
+}
+
+// Enqueues the status read-back, drains the stream and reports new flags.
+int sync_and_check(nbody_ctx *c)
+{
+    NB_CUDA(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->s),
+            "status read-back");
+    NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+    return absorb_status(c);
+}
+
+int ensure_partials(nbody_ctx *c, size_t bytes)
+{
+    if (bytes <= c->partials_cap) return NBODY_OK;
+    if (c->partials) {
+        NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+        cudaFree(c->partials);
+        c->partials = nullptr;
+        c->partials_cap = 0;
+    }
+    const size_t cap = std::max(bytes, static_cast<size_t>(1) << 20);
+    NB_CUDA(dev_alloc(&c->partials, cap), "partial-sum scratch allocation");
+    c->partials_cap = cap;
+    return NBODY_OK;
+}
+
+// Force on a device list already in act_force.
+int force_internal(nbody_ctx *c, int64_t n_act)
+{
+    ForceConfig cfg{};
+    const int r = force_choose(c->p.mode, n_act, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
+                               &cfg);
+    if (r != NBODY_OK) return fail(r, "unsupported force shape: %d threads x %d i per thread", c->p.j_tile, c->p.i_block);
+    const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, cfg, n_act));
+    if (rp != NBODY_OK) return rp;
+    int64_t launches = 0;
+    NB_CUDA(force_launch(c->p.mode, c->J, c->n, c->act_force, n_act, static_cast<float>(c->eps2), cfg,
+                         c->f_acc, c->f_jerk, c->f_pot, c->partials, c->st, c->s, &launches),
+            "force kernel launch");
+    c->stats.kernel_launches += launches;
+    c->stats.force_calls += 1;
+    c->stats.pairs += n_act * (c->n - 1);
+    c->stats.last_threads = cfg.threads;
+    c->stats.last_i_per_thread = cfg.ipt;
+    c->stats.last_j_split = cfg.split;
+    c->force_n_act = n_act;
+    return NBODY_OK;
+}
+
+int predict_internal(nbody_ctx *c, int64_t tick)
+{
+    if (tick < c->t_max)
+        return fail(NBODY_EINVAL, "prediction time %lld ticks is before a particle time %lld",
+                    static_cast<long long>(tick), static_cast<long long>(c->t_max));
+    NB_CUDA(predict_launch(c->S, c->J, tick, c->p.lmax, c->p.mode == kModeComp, c->s, &c->stats.kernel_launches),
+            "predictor launch");
+    c->t_pred = tick;
+    c->pred_valid = true;
+    c->force_n_act = -1;
+    return NBODY_OK;
+}
+
+int correct_internal(nbody_ctx *c, const int32_t *act_dev, int64_t n_act, const double *acc_dev,
+                     const double *jerk_dev)
+{
+    NB_CUDA(correct_launch(c->S, act_dev, n_act, acc_dev, jerk_dev, c->t_pred, c->p.eta, c->p.lmin, c->p.lmax,
+                           c->st, c->s, &c->stats.kernel_launches),
+            "corrector launch");
+    if (n_act > 0) {
+        c->t_max = std::max(c->t_max, c->t_pred);
+        c->stats.blocks += 1;
+    }
+    c->pred_valid = false;  // the corrected particles moved: predict again before the next force
+    c->force_n_act = -1;
+    return NBODY_OK;
+}
+
+int schedule_internal(nbody_ctx *c, int64_t *t_blk, int64_t *n_act)
+{
+    NB_CUDA(schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, c->s,
+                            &c->stats.kernel_launches),
+            "scheduler launch");
+    NB_CUDA(cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, c->s),
+            "schedule read-back");
+    const int r = sync_and_check(c);
+    if (r != NBODY_OK) return r;
+    *t_blk = c->sched_host->t_blk;
+    *n_act = c->sched_host->n_act;
+    return NBODY_OK;
+}
+
+int check_params(const nbody_params *p)
+{
+    if (!(p->eta > 0.0) || !std::isfinite(p->eta)) return fail(NBODY_EINVAL, "eta must be positive");
+    if (p->lmin < 0 || p->lmax > 40 || p->lmin > p->lmax)
+        return fail(NBODY_EINVAL, "need 0 <= lmin <= lmax <= 40 (got %d, %d)", p->lmin, p->lmax);
+    if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP) return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
+    if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256)
+        return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128 or 256");
+    if (p->i_block != 0 && p->i_block != 1 && p->i_block != 2 && p->i_block != 4)
+        return fail(NBODY_EINVAL, "i_block must be 0, 1, 2 or 4");
+    if (p->j_split < 0) return fail(NBODY_EINVAL, "j_split must be >= 0");
+    return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nbody_default_params(nbody_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->eta = 0.01;
+    p->eta_init = 0.0;
+    p->lmin = 6;
+    p->lmax = 26;
+    p->mode = NBODY_MODE_PLAIN;
+}
+
+int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, const double *v, double eps2,
+               const nbody_params *p)
+{
+    g_err[0] = '\0';
+    if (!out || !m || !x || !v) return fail(NBODY_EINVAL, "nbody_init: null pointer argument");
+    *out = nullptr;
+    if (n < 1 || n > 2147483647LL) return fail(NBODY_EINVAL, "nbody_init: n = %lld out of range", static_cast<long long>(n));
+    if (!(eps2 >= 0.0) || !std::isfinite(eps2)) return fail(NBODY_EINVAL, "nbody_init: eps2 must be finite and >= 0");
+    nbody_params prm;
+    if (p) prm = *p;
+    else nbody_default_params(&prm);
+    int r = check_params(&prm);
+    if (r != NBODY_OK) return r;
+    if (prm.eta_init <= 0.0) prm.eta_init = prm.eta;
+
+    nbody_ctx *c = new (std::nothrow) nbody_ctx;
+    if (!c) return fail(NBODY_ENOMEM, "nbody_init: host allocation failed");
+    c->n = n;
+    c->n_pad = (n + kJTile - 1) / kJTile * kJTile;
+    c->eps2 = eps2;
+    c->p = prm;
+    c->s = static_cast<cudaStream_t>(prm.stream);
+
+    auto bail = [&](int code) {
+        release(c);
+        return code;
+    };
+#define NB_INIT(call, what)                        \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, what)); \
+    } while (0)
+
+    int dev = 0;
+    NB_INIT(cudaGetDevice(&dev), "cudaGetDevice");
+    NB_INIT(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const size_t nd = static_cast<size_t>(n);
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->state), 13 * nd * sizeof(double)), "state allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->t), nd * sizeof(int64_t)), "time allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->level), nd), "level allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->jbuf), 3 * static_cast<size_t>(c->n_pad) * sizeof(float4)),
+            "j-stream allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_force), nd * sizeof(int32_t)), "list allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_corr), nd * sizeof(int32_t)), "list allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_sched), nd * sizeof(int32_t)), "list allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->f_acc), 3 * nd * sizeof(double)), "force allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->f_jerk), 3 * nd * sizeof(double)), "force allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->f_pot), nd * sizeof(double)), "force allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->stage), 6 * nd * sizeof(double)), "staging allocation");
+    NB_INIT(dev_alloc(&c->sched_scratch, sched_scratch_bytes(n)), "scheduler scratch allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->sched_out), sizeof(SchedOut)), "scheduler allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->st), sizeof(DevStatus)), "status allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->phi), nd * sizeof(double)), "energy scratch allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->e_out), 2 * sizeof(double)), "energy allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->trange), 2 * sizeof(unsigned long long)), "time-range allocation");
+    NB_INIT(host_alloc(reinterpret_cast<void **>(&c->sched_host), sizeof(SchedOut)), "pinned allocation");
+    NB_INIT(host_alloc(reinterpret_cast<void **>(&c->st_host), sizeof(DevStatus)), "pinned allocation");
+    NB_INIT(host_alloc(reinterpret_cast<void **>(&c->e_host), 2 * sizeof(double)), "pinned allocation");
+    NB_INIT(host_alloc(reinterpret_cast<void **>(&c->trange_host), 2 * sizeof(unsigned long long)),
+            "pinned allocation");
+    std::memset(c->st_host, 0, sizeof(DevStatus));
+
+    State &S = c->S;
+    S.n = n;
+    S.m = c->state;
+    for (int q = 0; q < 3; ++q) {
+        S.x[q] = c->state + (1 + q) * nd;
+        S.v[q] = c->state + (4 + q) * nd;
+        S.a[q] = c->state + (7 + q) * nd;
+        S.k[q] = c->state + (10 + q) * nd;
+    }
+    S.t = c->t;
+    S.level = c->level;
+    c->J.posm = c->jbuf;
+    c->J.vel = c->jbuf + c->n_pad;
+    c->J.poslo = c->jbuf + 2 * c->n_pad;
+    c->J.n_pad = c->n_pad;
+
+    cudaStream_t s = c->s;
+    int64_t *L = &c->stats.kernel_launches;
+    NB_INIT(cudaMemsetAsync(c->jbuf, 0, 3 * static_cast<size_t>(c->n_pad) * sizeof(float4), s), "memset");
+    NB_INIT(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s), "memset");
+    NB_INIT(cudaMemsetAsync(c->state + 7 * nd, 0, 6 * nd * sizeof(double), s), "memset");
+    NB_INIT(cudaMemsetAsync(c->t, 0, nd * sizeof(int64_t), s), "memset");
+    NB_INIT(to_device(c->state, m, nd * sizeof(double), s), "mass upload");
+    NB_INIT(to_device(c->stage, x, 3 * nd * sizeof(double), s), "position upload");
+    NB_INIT(aos_to_soa_launch(c->stage, S.x[0], S.x[1], S.x[2], n, s, L), "layout kernel");
+    NB_INIT(to_device(c->stage + 3 * nd, v, 3 * nd * sizeof(double), s), "velocity upload");
+    NB_INIT(aos_to_soa_launch(c->stage + 3 * nd, S.v[0], S.v[1], S.v[2], n, s, L), "layout kernel");
+
+    // t = 0: predicted state = state; full force; first levels.
+    r = predict_internal(c, 0);
+    if (r != NBODY_OK) return bail(r);
+    NB_INIT(iota_launch(c->act_force, n, s, L), "index kernel");
+    r = force_internal(c, n);
+    if (r != NBODY_OK) return bail(r);
+    NB_INIT(init_levels_launch(S, c->f_acc, c->f_jerk, c->p.eta_init, c->p.lmin, c->p.lmax, c->st, s, L),
+            "initial level kernel");
+    c->force_n_act = -1;
+    c->pred_valid = false;
+    c->t_max = 0;
+    r = sync_and_check(c);
+    if (r == NBODY_EDTMIN) r = NBODY_OK;  // the first steps may be clamped; counted, not fatal here
+    if (r != NBODY_OK) return bail(r);
+    c->stats.n = n;
+    c->stats.n_pad = c->n_pad;
+    c->stats.mode = c->p.mode;
+#undef NB_INIT
+    *out = c;
+    return NBODY_OK;
+}
+
+int nbody_next_block(nbody_ctx *c, double *t_blk, int64_t *n_act, int32_t *active)
+{
+    if (!c || !t_blk || !n_act) return fail(NBODY_EINVAL, "nbody_next_block: null argument");
+    int64_t tb = 0, na = 0;
+    int r = schedule_internal(c, &tb, &na);
+    if (r != NBODY_OK) return r;
+    *t_blk = std::ldexp(static_cast<double>(tb), -c->p.lmax);
+    *n_act = na;
+    if (active && na > 0) {
+        NB_CUDA(cudaMemcpyAsync(active, c->act_sched, static_cast<size_t>(na) * sizeof(int32_t), cudaMemcpyDefault,
+                                c->s),
+                "active list copy");
+        if (!is_device_ptr(active)) NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+    }
+    return NBODY_OK;
+}
+
+int nbody_predict(nbody_ctx *c, double t)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_predict: null context");
+    int64_t tick;
+    const int r = to_ticks(c, t, &tick);
+    if (r != NBODY_OK) return r;
+    return predict_internal(c, tick);
+}
+
+int nbody_force(nbody_ctx *c, const int32_t *active, int64_t n_act, double *acc, double *jerk, double *pot)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_force: null context");
+    if (n_act < 0 || n_act > c->n) return fail(NBODY_EINVAL, "nbody_force: n_act = %lld outside [0, n]", static_cast<long long>(n_act));
+    if (n_act > 0 && !active) return fail(NBODY_EINVAL, "nbody_force: null active list");
+    if (!c->pred_valid) return fail(NBODY_ESTATE, "nbody_force: no prediction since the last correction");
+    const size_t na = static_cast<size_t>(n_act);
+    NB_CUDA(to_device(c->act_force, active, na * sizeof(int32_t), c->s), "active list upload");
+    int r = force_internal(c, n_act);
+    if (r != NBODY_OK) return r;
+    bool host_out = false;
+    if (acc) {
+        NB_CUDA(cudaMemcpyAsync(acc, c->f_acc, 3 * na * sizeof(double), cudaMemcpyDefault, c->s), "acc copy");
+        host_out |= !is_device_ptr(acc);
+    }
+    if (jerk) {
+        NB_CUDA(cudaMemcpyAsync(jerk, c->f_jerk, 3 * na * sizeof(double), cudaMemcpyDefault, c->s), "jerk copy");
+        host_out |= !is_device_ptr(jerk);
+    }
+    if (pot) {
+        NB_CUDA(cudaMemcpyAsync(pot, c->f_pot, na * sizeof(double), cudaMemcpyDefault, c->s), "pot copy");
+        host_out |= !is_device_ptr(pot);
+    }
+    if (host_out) {
+        r = sync_and_check(c);
+        if (r != NBODY_OK) return r;
+    }
+    return NBODY_OK;
+}
+
+int nbody_correct(nbody_ctx *c, const int32_t *active, int64_t n_act, const double *acc, const double *jerk)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_correct: null context");
+    if (n_act < 0 || n_act > c->n) return fail(NBODY_EINVAL, "nbody_correct: n_act = %lld outside [0, n]", static_cast<long long>(n_act));
+    if (n_act > 0 && !active) return fail(NBODY_EINVAL, "nbody_correct: null active list");
+    if ((acc == nullptr) != (jerk == nullptr)) return fail(NBODY_EINVAL, "nbody_correct: give both acc and jerk, or neither");
+    if (!c->pred_valid) return fail(NBODY_ESTATE, "nbody_correct: no prediction to correct from");
+    const size_t na = static_cast<size_t>(n_act);
+    const double *fa = c->f_acc, *fj = c->f_jerk;
+    if (!acc) {
+        if (c->force_n_act != n_act)
+            return fail(NBODY_ESTATE, "nbody_correct: the last nbody_force had %lld rows, not %lld",
+                        static_cast<long long>(c->force_n_act), static_cast<long long>(n_act));
+    } else {
+        NB_CUDA(to_device(c->stage, acc, 3 * na * sizeof(double), c->s), "acc upload");
+        NB_CUDA(to_device(c->stage + 3 * c->n, jerk, 3 * na * sizeof(double), c->s), "jerk upload");
+        fa = c->stage;
+        fj = c->stage + 3 * c->n;
+    }
+    NB_CUDA(to_device(c->act_corr, active, na * sizeof(int32_t), c->s), "active list upload");
+    return correct_internal(c, c->act_corr, n_act, fa, fj);
+}
+
+int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_step: null context");
+    int64_t tend;
+    int r = to_ticks(c, t_end, &tend);
+    if (r != NBODY_OK) return r;
+    const int64_t dtmax = int64_t(1) << (c->p.lmax - c->p.lmin);
+    if (tend % dtmax != 0) return fail(NBODY_EINVAL, "nbody_step: t_end must be a multiple of dt_max = 2^-%d", c->p.lmin);
+    if (tend < c->t_max) return fail(NBODY_EINVAL, "nbody_step: t_end is before the current time");
+    int64_t done = 0;
+    for (;;) {
+        if (max_steps > 0 && done >= max_steps) break;
+        int64_t tb, na;
+        r = schedule_internal(c, &tb, &na);
+        if (r != NBODY_OK) break;
+        if (tb > tend) break;
+        r = predict_internal(c, tb);
+        if (r != NBODY_OK) break;
+        NB_CUDA(cudaMemcpyAsync(c->act_force, c->act_sched, static_cast<size_t>(na) * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, c->s),
+                "list copy");
+        r = force_internal(c, na);
+        if (r != NBODY_OK) break;
+        r = correct_internal(c, c->act_sched, na, c->f_acc, c->f_jerk);
+        if (r != NBODY_OK) break;
+        ++done;
+    }
+    if (n_steps) *n_steps = done;
+    if (r != NBODY_OK) return r;
+    return sync_and_check(c);
+}
+
+int nbody_sync(nbody_ctx *c)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_sync: null context");
+    return sync_and_check(c);
+}
+
+int nbody_energy(nbody_ctx *c, double *ekin, double *epot)
+{
+    if (!c || !ekin || !epot) return fail(NBODY_EINVAL, "nbody_energy: null argument");
+    NB_CUDA(time_range_launch(c->S, c->trange, c->s, &c->stats.kernel_launches), "time-range kernel");
+    NB_CUDA(cudaMemcpyAsync(c->trange_host, c->trange, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s),
+            "time-range read-back");
+    int r = sync_and_check(c);
+    if (r != NBODY_OK) return r;
+    if (c->trange_host[0] != c->trange_host[1])
+        return fail(NBODY_ENOTSYNC, "particles are at different times (%llu .. %llu ticks)", c->trange_host[0],
+                    c->trange_host[1]);
+    NB_CUDA(energy_launch(c->S, c->eps2, c->phi, c->e_out, c->s, &c->stats.kernel_launches), "energy kernels");
+    NB_CUDA(cudaMemcpyAsync(c->e_host, c->e_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s), "energy read-back");
+    r = sync_and_check(c);
+    if (r != NBODY_OK) return r;
+    *ekin = c->e_host[0];
+    *epot = c->e_host[1];
+    return NBODY_OK;
+}
+
+int nbody_get_state(nbody_ctx *c, double *x, double *v, double *a, double *k, int64_t *t_tick, int8_t *level)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_get_state: null context");
+    const size_t nd = static_cast<size_t>(c->n);
+    double *const *src[4] = {c->S.x, c->S.v, c->S.a, c->S.k};
+    double *dst[4] = {x, v, a, k};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        double *tmp = c->stage + (q & 1) * 3 * nd;
+        NB_CUDA(soa_to_aos_launch(src[q][0], src[q][1], src[q][2], tmp, c->n, c->s, &c->stats.kernel_launches),
+                "layout kernel");
+        NB_CUDA(cudaMemcpyAsync(dst[q], tmp, 3 * nd * sizeof(double), cudaMemcpyDefault, c->s), "state copy");
+    }
+    if (t_tick) NB_CUDA(cudaMemcpyAsync(t_tick, c->t, nd * sizeof(int64_t), cudaMemcpyDefault, c->s), "time copy");
+    if (level) NB_CUDA(cudaMemcpyAsync(level, c->level, nd, cudaMemcpyDefault, c->s), "level copy");
+    return sync_and_check(c);
+}
+
+int nbody_set_state(nbody_ctx *c, const double *x, const double *v, const double *a, const double *k,
+                    const int64_t *t_tick, const int8_t *level)
+{
+    if (!c || !x || !v || !a || !k || !t_tick || !level) return fail(NBODY_EINVAL, "nbody_set_state: null argument");
+    const size_t nd = static_cast<size_t>(c->n);
+    std::vector<int64_t> th(nd);
+    std::vector<int8_t> lh(nd);
+    NB_CUDA(cudaMemcpy(th.data(), t_tick, nd * sizeof(int64_t), cudaMemcpyDefault), "time read");
+    NB_CUDA(cudaMemcpy(lh.data(), level, nd, cudaMemcpyDefault), "level read");
+    int64_t tmax = 0;
+    for (size_t i = 0; i < nd; ++i) {
+        const int L = lh[i];
+        if (L < c->p.lmin || L > c->p.lmax) return fail(NBODY_EINVAL, "nbody_set_state: level[%zu] = %d out of range", i, L);
+        const int64_t step = int64_t(1) << (c->p.lmax - L);
+        if (th[i] < 0 || th[i] % step != 0)
+            return fail(NBODY_EINVAL, "nbody_set_state: t_tick[%zu] is not a multiple of its step", i);
+        tmax = std::max(tmax, th[i]);
+    }
+    NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+    const double *srcs[4] = {x, v, a, k};
+    double **dsts[4] = {c->S.x, c->S.v, c->S.a, c->S.k};
+    for (int q = 0; q < 4; ++q) {
+        double *tmp = c->stage + (q & 1) * 3 * nd;
+        NB_CUDA(to_device(tmp, srcs[q], 3 * nd * sizeof(double), c->s), "state upload");
+        NB_CUDA(aos_to_soa_launch(tmp, dsts[q][0], dsts[q][1], dsts[q][2], c->n, c->s, &c->stats.kernel_launches),
+                "layout kernel");
+    }
+    NB_CUDA(cudaMemcpyAsync(c->t, th.data(), nd * sizeof(int64_t), cudaMemcpyHostToDevice, c->s), "time upload");
+    NB_CUDA(cudaMemcpyAsync(c->level, lh.data(), nd, cudaMemcpyHostToDevice, c->s), "level upload");
+    c->t_max = tmax;
+    c->pred_valid = false;
+    c->force_n_act = -1;
+    return sync_and_check(c);
+}
+
+int nbody_get_predicted(nbody_ctx *c, float *posm, float *vel, float *poslo)
+{
+    if (!c) return fail(NBODY_EINVAL, "nbody_get_predicted: null context");
+    if (!c->pred_valid) return fail(NBODY_ESTATE, "nbody_get_predicted: no current prediction");
+    const size_t bytes = static_cast<size_t>(c->n) * sizeof(float4);
+    if (posm) NB_CUDA(cudaMemcpyAsync(posm, c->J.posm, bytes, cudaMemcpyDefault, c->s), "j-stream copy");
+    if (vel) NB_CUDA(cudaMemcpyAsync(vel, c->J.vel, bytes, cudaMemcpyDefault, c->s), "j-stream copy");
+    if (poslo) NB_CUDA(cudaMemcpyAsync(poslo, c->J.poslo, bytes, cudaMemcpyDefault, c->s), "j-stream copy");
+    return sync_and_check(c);
+}
+
+int nbody_get_stats(nbody_ctx *c, nbody_stats *s)
+{
+    if (!c || !s) return fail(NBODY_EINVAL, "nbody_get_stats: null argument");
+    NB_CUDA(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->s), "status read-back");
+    NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+    c->stats.below_dt_min = static_cast<int64_t>(c->st_host->below_min);
+    c->stats.nonfinite = static_cast<int64_t>(c->st_host->nonfinite);
+    *s = c->stats;
+    return NBODY_OK;
+}
+
+void nbody_free(nbody_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->s);
+    release(c);
+}
+
+const char *nbody_strerror(int code)
+{
+    switch (code) {
+    case NBODY_OK: return "success";
+    case NBODY_EINVAL: return "invalid argument";
+    case NBODY_ENOMEM: return "out of memory";
+    case NBODY_ECUDA: return "CUDA runtime error";
+    case NBODY_EDTMIN: return "time step below dt_min";
+    case NBODY_ENONFINITE: return "non-finite force or state";
+    case NBODY_ENOTSYNC: return "particles not at a common time";
+    case NBODY_ETIMEOUT: return "device-side wait timed out";
+    case NBODY_ESTATE: return "call out of order";
+    default: return "unknown error code";
+    }
+}
+
+const char *nbody_last_error(void) { return g_err; }
+
+void nbody_debug_fail_alloc(int k) { g_fail_alloc = k > 0 ? k : 0; }
+
+void nbody_debug_skip_tile_copy(int on) { nb::g_skip_first_copy = on ? 1 : 0; }
+
+}  // extern "C"

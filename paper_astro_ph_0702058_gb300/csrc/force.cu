@@ -1,0 +1,129 @@
+// Launch-shape choice and launch of the force evaluation (kernels in force_impl.cuh).
+#include <algorithm>
+#include <cmath>
+
+#include "force_impl.cuh"
+
+namespace nb {
+
+cudaError_t force_dispatch_plain(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s);
+cudaError_t force_dispatch_comp(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s);
+int force_occupancy_plain(int threads, int ipt);
+int force_occupancy_comp(int threads, int ipt);
+cudaError_t reduce_plain(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
+                         cudaStream_t s);
+cudaError_t reduce_comp(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
+                        cudaStream_t s);
+
+int g_skip_first_copy = 0;  // test hook (nbody_debug_skip_tile_copy)
+
+namespace {
+
+int shape_index(int threads, int ipt)
+{
+    const int ti = threads == 64 ? 0 : threads == 128 ? 1 : threads == 256 ? 2 : -1;
+    const int ii = ipt == 1 ? 0 : ipt == 2 ? 1 : ipt == 4 ? 2 : -1;
+    return (ti < 0 || ii < 0) ? -1 : ti * 3 + ii;
+}
+
+// Resident blocks per SM of each compiled kernel (queried once per process;
+// every device this library runs on is the same sm_103 part).
+int occupancy(int mode, int threads, int ipt)
+{
+    static int cache[2][9];
+    static bool filled[2][9];
+    const int si = shape_index(threads, ipt);
+    if (si < 0) return 0;
+    if (!filled[mode][si]) {
+        cache[mode][si] = mode == kModeComp ? force_occupancy_comp(threads, ipt) : force_occupancy_plain(threads, ipt);
+        filled[mode][si] = true;
+    }
+    return cache[mode][si];
+}
+
+}  // namespace
+
+int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_threads, int req_ipt,
+                 int req_split, ForceConfig *cfg)
+{
+    const int n_tiles = static_cast<int>(n_pad / kJTile);
+    int threads = req_threads;
+    int ipt = req_ipt;
+    if (threads == 0) threads = n_act >= 8192 ? 128 : 64;
+    if (ipt == 0) ipt = n_act >= static_cast<int64_t>(sm_count) * 128 * 2 * 2 ? 2 : 1;
+    if (shape_index(threads, ipt) < 0) return NBODY_EINVAL;
+    const int per = threads * ipt;
+    const int n_iblk = static_cast<int>(std::max<int64_t>(1, (n_act + per - 1) / per));
+    int split = req_split;
+    if (split <= 0) {
+        // At least one full wave of blocks; among a few larger splits take the
+        // one whose last wave is fullest (fewer idle SMs at the end).
+        const int slots = sm_count * std::max(1, occupancy(mode, threads, ipt));
+        const int smin = std::max(1, (slots + n_iblk - 1) / n_iblk);
+        auto eff = [&](int s) {
+            const double waves = static_cast<double>(n_iblk) * s / slots;
+            return waves / std::ceil(waves);
+        };
+        split = smin;
+        double best = eff(smin);
+        for (int s = smin + 1; s <= smin + 15; ++s) {
+            const double e = eff(s);
+            if (e > best + 0.02) {
+                best = e;
+                split = s;
+            }
+        }
+    }
+    split = std::max(1, std::min(split, n_tiles));
+    const int tps = (n_tiles + split - 1) / split;
+    split = (n_tiles + tps - 1) / tps;
+    cfg->threads = threads;
+    cfg->ipt = ipt;
+    cfg->split = split;
+    cfg->tiles_per_split = tps;
+    cfg->n_iblk = n_iblk;
+    return NBODY_OK;
+}
+
+size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
+{
+    if (cfg.split <= 1) return 0;
+    const size_t nc = mode == kModeComp ? 14 : 7;
+    return static_cast<size_t>(cfg.split) * nc * static_cast<size_t>(n_act) * sizeof(float);
+}
+
+cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active, int64_t n_act, float eps2,
+                         const ForceConfig &cfg, double *acc, double *jerk, double *pot, void *partials,
+                         DevStatus *st, cudaStream_t s, int64_t *launches)
+{
+    if (n_act <= 0) return cudaSuccess;
+    const ForceConfig &c = cfg;
+    ForceParams P;
+    P.posm = js.posm;
+    P.vel = js.vel;
+    P.poslo = js.poslo;
+    P.active = active;
+    P.n_act = static_cast<int>(n_act);
+    P.n = static_cast<int>(n);
+    P.n_tiles = static_cast<int>(js.n_pad / kJTile);
+    P.tiles_per_split = c.tiles_per_split;
+    P.eps2 = eps2;
+    P.acc = acc;
+    P.jerk = jerk;
+    P.pot = pot;
+    P.part = static_cast<float *>(partials);
+    P.st = st;
+    P.skip_first_copy = g_skip_first_copy;
+    cudaError_t e = mode == kModeComp ? force_dispatch_comp(P, c, s) : force_dispatch_plain(P, c, s);
+    if (e != cudaSuccess) return e;
+    ++*launches;
+    if (c.split > 1) {
+        e = mode == kModeComp ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s)
+                              : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s);
+        if (e != cudaSuccess) return e;
+        ++*launches;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace nb

@@ -1,0 +1,400 @@
+// Direct-summation acceleration, jerk and potential (Eq. Force with the
+// softened pair term of Appendix A of Portegies Zwart, Belleman & Geldof
+// 2007), FP32 pair arithmetic on the FP32 j-stream.
+//
+// Kernel layout (one launch):
+//   grid  = (i-blocks, j-ranges); block = NT threads; each thread owns IPT
+//           active particles (rows q = blockIdx.x*NT*IPT + u*NT + threadIdx.x)
+//           and keeps their position/velocity and sums in registers.
+//   j     = the block's j-range is streamed through shared memory in tiles of
+//           kJTile particles, double-buffered: one thread issues bulk async
+//           (TMA) copies of the next tile while all threads work on the
+//           current one; completion is tracked by an mbarrier per buffer.
+//           Every thread reads the same j at the same time (shared-memory
+//           broadcast), so the loop is bound by the FP32 pipe.
+//   sums  = per PF pairs, fresh FP32 partial sums; each partial is then
+//           folded into the running total: an FP32 add (plain mode) or Knuth's
+//           TwoSum into a (hi, lo) double-single pair (compensated mode).
+//   split = with more than one j-range, each range writes its sums to scratch
+//           and a second kernel adds the ranges in a fixed order (FP64), so
+//           results never depend on scheduling.
+// The self pair j = i is excluded exactly (Eq. Force sums over j != i): a
+// thread whose own i lies in the current tile runs a copy of the tile loop
+// that zeroes the term with j == i; all other tiles run without the test.
+// This also makes eps2 = 0 safe (r = 0 occurs only for j = i).
+#pragma once
+
+#include "nbody_internal.cuh"
+#include "ptx.cuh"
+
+namespace nb {
+
+struct ForceParams {
+    const float4 *__restrict__ posm;
+    const float4 *__restrict__ vel;
+    const float4 *__restrict__ poslo;
+    const int32_t *__restrict__ active;
+    int n_act;
+    int n;
+    int n_tiles;
+    int tiles_per_split;
+    float eps2;
+    double *__restrict__ acc;
+    double *__restrict__ jerk;
+    double *__restrict__ pot;
+    float *__restrict__ part;  // [split][7 or 14][n_act] when split > 1
+    DevStatus *st;
+    int skip_first_copy;       // test hook: leave the first tile's copy out
+};
+
+// One pair term, Appendix A: dx = x_j - x_i, dv = v_j - v_i, r^2 = eps^2 + dx.dx,
+// a += m r^-3 dx, k += m r^-3 (dv - 3 (dx.dv) r^-2 dx), phi -= m r^-1.
+// Compensated mode forms dx from the hi/lo splits of the FP64 positions.
+// 27 FP32 operations + 1 MUFU rsqrt (plain); 33 + 1 (compensated).
+template <int MODE, bool SELF>
+__device__ __forceinline__ void pair_term(const float4 pj, const float4 vj, const float4 lj,
+                                          const float4 xi, const float4 vi, const float4 li,
+                                          const float eps2, const int j, const int i, float (&p)[7])
+{
+    float dx, dy, dz;
+    if (MODE == kModeComp) {
+        dx = (pj.x - xi.x) + (lj.x - li.x);
+        dy = (pj.y - xi.y) + (lj.y - li.y);
+        dz = (pj.z - xi.z) + (lj.z - li.z);
+    } else {
+        dx = pj.x - xi.x;
+        dy = pj.y - xi.y;
+        dz = pj.z - xi.z;
+    }
+    const float dvx = vj.x - vi.x;
+    const float dvy = vj.y - vi.y;
+    const float dvz = vj.z - vi.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    float rinv = rsqrt_mufu(r2);
+    if (SELF) rinv = (j == i) ? 0.0f : rinv;  // j = i contributes nothing
+    const float xv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
+    const float rinv2 = rinv * rinv;
+    const float mr = pj.w * rinv;
+    const float mr3 = mr * rinv2;
+    const float w = 3.0f * (xv * rinv2);
+    p[0] = fmaf(mr3, dx, p[0]);
+    p[1] = fmaf(mr3, dy, p[1]);
+    p[2] = fmaf(mr3, dz, p[2]);
+    p[3] = fmaf(mr3, fmaf(-w, dx, dvx), p[3]);
+    p[4] = fmaf(mr3, fmaf(-w, dy, dvy), p[4]);
+    p[5] = fmaf(mr3, fmaf(-w, dz, dvz), p[5]);
+    p[6] = p[6] - mr;
+}
+
+// Knuth's TwoSum (TAOCP vol. 2, 4.2.2): s + e == hi + x exactly; the error is
+// kept in lo, so (hi, lo) carries ~48 significant bits.
+__device__ __forceinline__ void fold_ds(float &hi, float &lo, const float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo = lo + e;
+}
+
+// Sums over one staged tile of kJTile j (starting at global index j0).
+template <int MODE, int IPT, int PF, bool SELF>
+__device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, const float4 *sl, const int j0,
+                                          const float4 (&xi)[IPT], const float4 (&vi)[IPT],
+                                          const float4 (&li)[IPT], const int (&gi)[IPT], const float eps2,
+                                          float (&tot)[IPT][7], float (&lo)[IPT][7])
+{
+#pragma unroll 1
+    for (int jb = 0; jb < kJTile; jb += PF) {
+        float p[IPT][7];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) p[u][c] = 0.0f;
+#pragma unroll 8
+        for (int jj = 0; jj < PF; ++jj) {
+            const float4 pj = sp[jb + jj];
+            const float4 vj = sv[jb + jj];
+            const float4 lj = (MODE == kModeComp) ? sl[jb + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+                pair_term<MODE, SELF>(pj, vj, lj, xi[u], vi[u], li[u], eps2, j0 + jb + jj, gi[u], p[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                if (MODE == kModeComp)
+                    fold_ds(tot[u][c], lo[u][c], p[u][c]);
+                else
+                    tot[u][c] += p[u][c];
+            }
+    }
+}
+
+template <int MODE, int NT, int IPT, int PF>
+__global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
+{
+    constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
+    constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
+    static_assert(kJTile % PF == 0, "fold length must divide the tile");
+    __shared__ __align__(128) float4 sj[2][NARR][kJTile];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int t_begin = blockIdx.y * P.tiles_per_split;
+    const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
+
+    float4 xi[IPT], vi[IPT], li[IPT];
+    int gi[IPT];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        int idx = -1;
+        if (q < P.n_act) {
+            idx = P.active[q];
+            if (idx < 0 || idx >= P.n) {
+                atomicOr(&P.st->flags, kFlagBadIndex);
+                P.st->bad_index = q;
+                idx = -1;
+            }
+        }
+        gi[u] = idx;
+        const int l = idx >= 0 ? idx : 0;
+        xi[u] = P.posm[l];
+        vi[u] = P.vel[l];
+        li[u] = (MODE == kModeComp) ? P.poslo[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    float tot[IPT][7], lo[IPT][7];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            tot[u][c] = 0.0f;
+            lo[u][c] = 0.0f;
+        }
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int b) {
+        mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
+        const size_t off = static_cast<size_t>(tile) * kJTile;
+        bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
+        bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
+        if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+    };
+
+    bool ok = true;
+    int it_stop = 0;
+    if (tid == 0 && t_begin < t_end && !P.skip_first_copy) issue(t_begin, 0);
+    for (int t = t_begin; t < t_end; ++t) {
+        const int it = t - t_begin;
+        const int b = it & 1;
+        if (tid == 0 && t + 1 < t_end) issue(t + 1, b ^ 1);
+        ok = mbar_wait_bounded(&bar[b], (it >> 1) & 1);
+        if (ok) {
+            const int j0 = t * kJTile;
+            bool self_tile = false;
+#pragma unroll
+            for (int u = 0; u < IPT; ++u) self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
+            if (self_tile)
+                tile_sums<MODE, IPT, PF, true>(sj[b][0], sj[b][1], sj[b][NARR - 1], j0, xi, vi, li, gi, P.eps2, tot, lo);
+            else
+                tile_sums<MODE, IPT, PF, false>(sj[b][0], sj[b][1], sj[b][NARR - 1], j0, xi, vi, li, gi, P.eps2, tot, lo);
+        }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            it_stop = it;
+            break;
+        }
+    }
+
+    if (!ok) {
+        // A tile never arrived.  Drain (with a bound) the copies this block
+        // may still have in flight, record the timeout and leave the outputs
+        // untouched; the host reports NBODY_ETIMEOUT.
+        if (tid == 0) {
+            const int b = it_stop & 1;
+            mbar_wait_bounded(&bar[b], (it_stop >> 1) & 1);
+            if (t_begin + it_stop + 1 < t_end) mbar_wait_bounded(&bar[b ^ 1], ((it_stop + 1) >> 1) & 1);
+            atomicOr(&P.st->flags, kFlagTimeout);
+        }
+        return;
+    }
+
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        if (q >= P.n_act) continue;
+        if (gridDim.y == 1) {
+            double r[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                r[c] = (MODE == kModeComp) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
+                                           : static_cast<double>(tot[u][c]);
+            double *pa = P.acc + 3 * static_cast<size_t>(q);
+            double *pk = P.jerk + 3 * static_cast<size_t>(q);
+            pa[0] = r[0];
+            pa[1] = r[1];
+            pa[2] = r[2];
+            pk[0] = r[3];
+            pk[1] = r[4];
+            pk[2] = r[5];
+            P.pot[q] = r[6];
+        } else {
+            constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+            float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * P.n_act + q;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                base[static_cast<size_t>(c) * P.n_act] = tot[u][c];
+                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * P.n_act] = lo[u][c];
+            }
+        }
+    }
+}
+
+// Adds the j-range partial sums of each row in ascending range order (FP64).
+template <int MODE>
+__global__ void reduce_partials_kernel(const float *__restrict__ part, int split, int n_act,
+                                       double *__restrict__ acc, double *__restrict__ jerk,
+                                       double *__restrict__ pot)
+{
+    constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_act) return;
+    double r[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double s = 0.0;
+        for (int sp = 0; sp < split; ++sp) {
+            const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
+            s += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
+            if (MODE == kModeComp) s += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
+        }
+        r[c] = s;
+    }
+    acc[3 * static_cast<size_t>(q) + 0] = r[0];
+    acc[3 * static_cast<size_t>(q) + 1] = r[1];
+    acc[3 * static_cast<size_t>(q) + 2] = r[2];
+    jerk[3 * static_cast<size_t>(q) + 0] = r[3];
+    jerk[3 * static_cast<size_t>(q) + 1] = r[4];
+    jerk[3 * static_cast<size_t>(q) + 2] = r[5];
+    pot[q] = r[6];
+}
+
+// Same sums for few rows and many j-ranges: one warp per row, lane l adds the
+// ranges l, l + 32, ... (FP64), then a fixed shuffle tree adds the 32 lanes.
+// Used when the one-thread-per-row version would walk hundreds of ranges.
+template <int MODE>
+__global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int split, int n_act,
+                                            double *__restrict__ acc, double *__restrict__ jerk,
+                                            double *__restrict__ pot)
+{
+    constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= n_act) return;
+    double r[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) r[c] = 0.0;
+    for (int sp = lane; sp < split; sp += 32) {
+        const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            r[c] += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
+            if (MODE == kModeComp) r[c] += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_down_sync(0xffffffffu, r[c], o);
+    if (lane == 0) {
+        acc[3 * static_cast<size_t>(q) + 0] = r[0];
+        acc[3 * static_cast<size_t>(q) + 1] = r[1];
+        acc[3 * static_cast<size_t>(q) + 2] = r[2];
+        jerk[3 * static_cast<size_t>(q) + 0] = r[3];
+        jerk[3 * static_cast<size_t>(q) + 1] = r[4];
+        jerk[3 * static_cast<size_t>(q) + 2] = r[5];
+        pot[q] = r[6];
+    }
+}
+
+// Fold length (pairs per FP32 partial) of each mode.
+template <int MODE>
+struct FoldLen {
+    static constexpr int value = 64;
+};
+
+template <int MODE, int NT, int IPT>
+cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+    dim3 grid(cfg.n_iblk, cfg.split);
+    force_kernel<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int MODE, int NT, int IPT>
+int occupancy_instance(int *blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
+                                                         NT, 0);
+}
+
+// Dispatch over the compiled shapes of one mode.
+template <int MODE>
+cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+#define NB_CASE(T, I) \
+    if (cfg.threads == T && cfg.ipt == I) return launch_force_instance<MODE, T, I>(P, cfg, s);
+    NB_CASE(64, 1)
+    NB_CASE(64, 2)
+    NB_CASE(64, 4)
+    NB_CASE(128, 1)
+    NB_CASE(128, 2)
+    NB_CASE(128, 4)
+    NB_CASE(256, 1)
+    NB_CASE(256, 2)
+    NB_CASE(256, 4)
+#undef NB_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <int MODE>
+int force_occupancy(int threads, int ipt)
+{
+    int b = 0;
+#define NB_CASE(T, I) \
+    if (threads == T && ipt == I) { occupancy_instance<MODE, T, I>(&b); return b; }
+    NB_CASE(64, 1)
+    NB_CASE(64, 2)
+    NB_CASE(64, 4)
+    NB_CASE(128, 1)
+    NB_CASE(128, 2)
+    NB_CASE(128, 4)
+    NB_CASE(256, 1)
+    NB_CASE(256, 2)
+    NB_CASE(256, 4)
+#undef NB_CASE
+    return 0;
+}
+
+template <int MODE>
+cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, double *jerk,
+                          double *pot, cudaStream_t s)
+{
+    const int nt = 256;
+    if (split >= 32 && n_act <= 8192)
+        reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+    else
+        reduce_partials_kernel<MODE><<<(n_act + nt - 1) / nt, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

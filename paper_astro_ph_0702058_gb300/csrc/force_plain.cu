@@ -1,0 +1,19 @@
+// Instantiates the force kernels of the plain mode (see force_impl.cuh).
+#include "force_impl.cuh"
+
+namespace nb {
+
+cudaError_t force_dispatch_plain(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+    return force_dispatch<kModePlain>(P, cfg, s);
+}
+
+int force_occupancy_plain(int threads, int ipt) { return force_occupancy<kModePlain>(threads, ipt); }
+
+cudaError_t reduce_plain(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
+                        cudaStream_t s)
+{
+    return reduce_launch<kModePlain>(part, split, n_act, acc, jerk, pot, s);
+}
+
+}  // namespace nb

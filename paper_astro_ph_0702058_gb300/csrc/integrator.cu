@@ -1,0 +1,509 @@
+// FP64 parts of the block-step Hermite integrator of Portegies Zwart,
+// Belleman & Geldof (2007), Sect. 2: predictor, corrector with the Aarseth
+// time step, power-of-two levels, the block scheduler, and the energy
+// diagnostic.  All of them are memory- or latency-bound; FP64 never enters
+// the O(N^2) pair loop (except in the energy diagnostic).
+#include <cfloat>
+
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int blocks_for(int64_t n, int threads, int cap = 1 << 20)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return static_cast<int>(b < cap ? b : cap);
+}
+
+// Predictor of Sect. 2 for one component, in Horner form with explicit
+// roundings so that the predictor and the corrector kernels give the same
+// bits:  x_p = x + dt (v + dt (a/2 + dt k/6)),  v_p = v + dt (a + dt k/2).
+__device__ __forceinline__ void predict_dim(double x, double v, double a, double k, double dt,
+                                            double &xp, double &vp)
+{
+    const double k6 = __dmul_rn(k, 1.0 / 6.0);
+    xp = __fma_rn(dt, __fma_rn(dt, __fma_rn(dt, k6, 0.5 * a), v), x);
+    vp = __fma_rn(dt, __fma_rn(dt, 0.5 * k, a), v);
+}
+
+__global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int comp)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double dt = static_cast<double>(t_new - S.t[i]) * tick;
+        double xp[3], vp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) predict_dim(S.x[c][i], S.v[c][i], S.a[c][i], S.k[c][i], dt, xp[c], vp[c]);
+        const float hx = __double2float_rn(xp[0]);
+        const float hy = __double2float_rn(xp[1]);
+        const float hz = __double2float_rn(xp[2]);
+        J.posm[i] = make_float4(hx, hy, hz, __double2float_rn(S.m[i]));
+        J.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
+        if (comp)
+            J.poslo[i] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
+                                     __double2float_rn(xp[1] - static_cast<double>(hy)),
+                                     __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+    }
+}
+
+__device__ __forceinline__ double norm3(const double *u)
+{
+    return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// Level L of the largest power of two 2^-L <= dt, clamped to [lmin, lmax];
+// returns -1 for NaN.  *clamped is set when dt < 2^-lmax (incl. dt <= 0).
+__device__ __forceinline__ int level_of(double dt, int lmin, int lmax, bool *clamped)
+{
+    *clamped = false;
+    if (isnan(dt)) return -1;
+    if (!(dt > 0.0)) {
+        *clamped = true;
+        return lmax;
+    }
+    if (isinf(dt)) return lmin;
+    int e;
+    frexp(dt, &e);  // dt = f 2^e with 1/2 <= f < 1, so 2^(e-1) <= dt < 2^e
+    int L = 1 - e;
+    if (L < lmin) L = lmin;
+    if (L > lmax) {
+        L = lmax;
+        *clamped = true;
+    }
+    return L;
+}
+
+// Corrector of Sect. 2 plus Eq. (timestep), one block row per thread.
+__global__ void correct_kernel(const State S, const int32_t *__restrict__ active, int64_t n_act,
+                               const double *__restrict__ acc, const double *__restrict__ jerk,
+                               int64_t t_new, double tick, double eta, int lmin, int lmax,
+                               DevStatus *st)
+{
+    const int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (q >= n_act) return;
+    const int64_t i = active[q];
+    if (i < 0 || i >= S.n) {
+        atomicOr(&st->flags, kFlagBadIndex);
+        st->bad_index = static_cast<int>(q);
+        return;
+    }
+    const double dt = static_cast<double>(t_new - S.t[i]) * tick;
+    const double idt = 1.0 / dt;
+    const double idt2 = idt * idt;
+    const double dt3 = dt * dt * dt;
+    const double dt4 = dt3 * dt;
+    double ap[3], kp[3], a2e[3], a3[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double a = S.a[c][i];
+        const double k = S.k[c][i];
+        double xp, vp;
+        predict_dim(S.x[c][i], S.v[c][i], a, k, dt, xp, vp);
+        ap[c] = acc[3 * q + c];
+        kp[c] = jerk[3 * q + c];
+        const double da = a - ap[c];  // Delta a = a - a_p
+        const double a2 = -6.0 * da * idt2 - (4.0 * k + 2.0 * kp[c]) * idt;
+        a3[c] = 12.0 * da * idt2 * idt + 6.0 * (k + kp[c]) * idt2;
+        const double xn = xp + dt4 * (a2 / 24.0 + a3[c] * dt / 120.0);
+        const double vn = vp + dt3 * (a2 / 6.0 + a3[c] * dt / 24.0);
+        a2e[c] = a2 + a3[c] * dt;  // a^(2) at the end of the step
+        finite = finite && isfinite(xn) && isfinite(vn) && isfinite(ap[c]) && isfinite(kp[c]);
+        S.x[c][i] = xn;
+        S.v[c][i] = vn;
+        S.a[c][i] = ap[c];
+        S.k[c][i] = kp[c];
+    }
+    // Eq. (timestep) with end-of-step quantities.
+    const double an = norm3(ap), kn = norm3(kp), a2n = norm3(a2e), a3n = norm3(a3);
+    const double num = an * a2n + kn * kn;
+    const double den = kn * a3n + a2n * a2n;
+    const double dtc = den == 0.0 ? static_cast<double>(INFINITY) : sqrt(eta * num / den);
+    bool clamped = false;
+    const int lc = level_of(dtc, lmin, lmax, &clamped);
+    const int l_old = S.level[i];
+    int l_new;
+    if (!finite || lc < 0) {
+        l_new = lmax;
+        atomicOr(&st->flags, kFlagNonfinite);
+        atomicAdd(&st->nonfinite, 1ull);
+    } else if (lc >= l_old) {
+        l_new = lc;  // shrink at once (or keep)
+    } else {
+        // grow one level, only if the new time is a multiple of twice the old step
+        const int64_t two_old = int64_t(2) << (lmax - l_old);
+        l_new = (l_old - 1 >= lmin && t_new % two_old == 0) ? l_old - 1 : l_old;
+    }
+    if (clamped) {
+        atomicOr(&st->flags, kFlagDtMin);
+        atomicAdd(&st->below_min, 1ull);
+    }
+    S.t[i] = t_new;
+    S.level[i] = static_cast<int8_t>(l_new);
+}
+
+// Start of a run: a, k from the full force at t = 0, t = 0 and the first level
+// from Eq. (initTimestep), dt = eta_init |a| / |k|.
+__global__ void init_levels_kernel(const State S, const double *__restrict__ acc,
+                                   const double *__restrict__ jerk, double eta_init, int lmin,
+                                   int lmax, DevStatus *st)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= S.n) return;
+    double a[3], k[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = acc[3 * i + c];
+        k[c] = jerk[3 * i + c];
+        S.a[c][i] = a[c];
+        S.k[c][i] = k[c];
+        finite = finite && isfinite(a[c]) && isfinite(k[c]);
+    }
+    const double kn = norm3(k);
+    const double dt0 = kn == 0.0 ? static_cast<double>(INFINITY) : eta_init * norm3(a) / kn;
+    bool clamped = false;
+    int L = level_of(dt0, lmin, lmax, &clamped);
+    if (!finite || L < 0) {
+        L = lmax;
+        atomicOr(&st->flags, kFlagNonfinite);
+        atomicAdd(&st->nonfinite, 1ull);
+    }
+    if (clamped) {
+        atomicOr(&st->flags, kFlagDtMin);
+        atomicAdd(&st->below_min, 1ull);
+    }
+    S.t[i] = 0;
+    S.level[i] = static_cast<int8_t>(L);
+}
+
+// ------------------------------------------------------------------ scheduler
+// Three passes over contiguous chunks (one per block): (1) per-chunk minimum
+// of t_i + dt_i, (2) global minimum and per-chunk match count, (3) ordered
+// compaction of the matching indices at the prefix offset of each chunk.
+struct SchedGeom {
+    int64_t chunk;
+    int blocks;
+};
+
+SchedGeom sched_geom(int64_t n)
+{
+    int64_t chunk = 2048;
+    if ((n + chunk - 1) / chunk > 1024) chunk = ((n + 1023) / 1024 + kThreads - 1) / kThreads * kThreads;
+    SchedGeom g;
+    g.chunk = chunk;
+    g.blocks = static_cast<int>((n + chunk - 1) / chunk);
+    if (g.blocks < 1) g.blocks = 1;
+    return g;
+}
+
+__device__ __forceinline__ unsigned long long due_tick(const State &S, int64_t i, int lmax)
+{
+    return static_cast<unsigned long long>(S.t[i] + (int64_t(1) << (lmax - S.level[i])));
+}
+
+// Block-wide reduction; `id` is the identity of `op` (pads missing warps).
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T *sh, T id)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = static_cast<int>(threadIdx.x) < nw ? sh[threadIdx.x] : id;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+struct MinOp {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
+};
+struct MaxOp {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; }
+};
+struct SumOp {
+    __device__ long long operator()(long long a, long long b) const { return a + b; }
+};
+
+__global__ void sched_min_kernel(const State S, int lmax, int64_t chunk, unsigned long long *bmin)
+{
+    __shared__ unsigned long long sh[32];
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = min(lo + chunk, S.n);
+    unsigned long long m = ~0ull;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const unsigned long long d = due_tick(S, i, lmax);
+        m = d < m ? d : m;
+    }
+    m = block_reduce(m, MinOp(), sh, ~0ull);
+    if (threadIdx.x == 0) bmin[blockIdx.x] = m;
+}
+
+__global__ void sched_count_kernel(const State S, int lmax, int64_t chunk, int nblk,
+                                   const unsigned long long *bmin, long long *bcnt, SchedOut *out)
+{
+    __shared__ unsigned long long shm[32];
+    __shared__ long long shc[32];
+    unsigned long long g = ~0ull;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) g = bmin[b] < g ? bmin[b] : g;
+    g = block_reduce(g, MinOp(), shm, ~0ull);
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = min(lo + chunk, S.n);
+    long long c = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += due_tick(S, i, lmax) == g;
+    c = block_reduce(c, SumOp(), shc, 0ll);
+    if (threadIdx.x == 0) {
+        bcnt[blockIdx.x] = c;
+        if (blockIdx.x == 0) out->t_blk = static_cast<long long>(g);
+    }
+}
+
+__global__ void sched_write_kernel(const State S, int lmax, int64_t chunk, int nblk,
+                                   const long long *bcnt, SchedOut *out, int32_t *active)
+{
+    __shared__ long long shc[32];
+    __shared__ int warp_tot[32];
+    const unsigned long long g = static_cast<unsigned long long>(out->t_blk);
+    long long off = 0, total = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        if (b < static_cast<int>(blockIdx.x)) off += bcnt[b];
+        total += bcnt[b];
+    }
+    off = block_reduce(off, SumOp(), shc, 0ll);
+    total = block_reduce(total, SumOp(), shc, 0ll);
+    if (blockIdx.x == 0 && threadIdx.x == 0) out->n_act = total;
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = min(lo + chunk, S.n);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool hit = i < hi && due_tick(S, i, lmax) == g;
+        const unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (l == 0) warp_tot[w] = __popc(mask);
+        __syncthreads();
+        int before = 0, round = 0;
+        for (int k = 0; k < nw; ++k) {
+            if (k < w) before += warp_tot[k];
+            round += warp_tot[k];
+        }
+        if (hit) active[off + before + __popc(mask & ((1u << l) - 1u))] = static_cast<int32_t>(i);
+        off += round;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ energy
+// phi_i = -sum_{j != i} m_j / sqrt(r^2 + eps^2) in FP64, j in ascending order.
+constexpr int kETile = 128;
+
+__global__ void phi_kernel(const State S, double eps2, double *__restrict__ phi)
+{
+    __shared__ double sx[kETile], sy[kETile], sz[kETile], sm[kETile];
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const bool live = i < S.n;
+    const double xi = live ? S.x[0][i] : 0.0;
+    const double yi = live ? S.x[1][i] : 0.0;
+    const double zi = live ? S.x[2][i] : 0.0;
+    double p = 0.0;
+    for (int64_t j0 = 0; j0 < S.n; j0 += kETile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kETile; t += blockDim.x) {
+            const int64_t j = j0 + t;
+            const bool ok = j < S.n;
+            sx[t] = ok ? S.x[0][j] : 0.0;
+            sy[t] = ok ? S.x[1][j] : 0.0;
+            sz[t] = ok ? S.x[2][j] : 0.0;
+            sm[t] = ok ? S.m[j] : 0.0;
+        }
+        __syncthreads();
+        const int jn = static_cast<int>(S.n - j0 < kETile ? S.n - j0 : kETile);
+        for (int t = 0; t < jn; ++t) {
+            if (j0 + t == i) continue;
+            const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
+            const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(eps2, __dmul_rn(dx, dx)), __dmul_rn(dy, dy)),
+                                        __dmul_rn(dz, dz));
+            p = __dsub_rn(p, __ddiv_rn(sm[t], __dsqrt_rn(r2)));
+        }
+    }
+    if (live) phi[i] = p;
+}
+
+// One block: E_kin = sum m v^2 / 2, E_pot = sum m phi / 2 (fixed summation order).
+__global__ void energy_sum_kernel(const State S, const double *__restrict__ phi, double *out)
+{
+    __shared__ double sk[1024], sp[1024];
+    double k = 0.0, p = 0.0;
+    for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) {
+        const double vx = S.v[0][i], vy = S.v[1][i], vz = S.v[2][i];
+        k += 0.5 * S.m[i] * (vx * vx + vy * vy + vz * vz);
+        p += 0.5 * S.m[i] * phi[i];
+    }
+    sk[threadIdx.x] = k;
+    sp[threadIdx.x] = p;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (static_cast<int>(threadIdx.x) < s) {
+            sk[threadIdx.x] += sk[threadIdx.x + s];
+            sp[threadIdx.x] += sp[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sk[0];
+        out[1] = sp[0];
+    }
+}
+
+__global__ void time_range_kernel(const State S, unsigned long long *out)
+{
+    __shared__ unsigned long long sh[32];
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const unsigned long long t = static_cast<unsigned long long>(S.t[i]);
+        lo = t < lo ? t : lo;
+        hi = t > hi ? t : hi;
+    }
+    lo = block_reduce(lo, MinOp(), sh, ~0ull);
+    hi = block_reduce(hi, MaxOp(), sh, 0ull);
+    if (threadIdx.x == 0) {
+        atomicMin(&out[0], lo);
+        atomicMax(&out[1], hi);
+    }
+}
+
+__global__ void aos_to_soa_kernel(const double *__restrict__ aos, double *c0, double *c1, double *c2, int64_t n)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        c0[i] = aos[3 * i];
+        c1[i] = aos[3 * i + 1];
+        c2[i] = aos[3 * i + 2];
+    }
+}
+
+__global__ void soa_to_aos_kernel(const double *c0, const double *c1, const double *c2, double *__restrict__ aos,
+                                  int64_t n)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        aos[3 * i] = c0[i];
+        aos[3 * i + 1] = c1[i];
+        aos[3 * i + 2] = c2[i];
+    }
+}
+
+__global__ void iota_kernel(int32_t *a, int64_t n)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        a[i] = static_cast<int32_t>(i);
+}
+
+}  // namespace
+
+cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches)
+{
+    iota_kernel<<<blocks_for(n, kThreads, 152 * 32), kThreads, 0, s>>>(a, n);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, bool comp,
+                           cudaStream_t s, int64_t *launches)
+{
+    predict_kernel<<<blocks_for(S.n, kThreads, 152 * 64), kThreads, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
+                                                                           comp ? 1 : 0);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act, const double *acc,
+                           const double *jerk, int64_t t_new, double eta, int lmin, int lmax, DevStatus *st,
+                           cudaStream_t s, int64_t *launches)
+{
+    if (n_act <= 0) return cudaSuccess;
+    correct_kernel<<<blocks_for(n_act, 128), 128, 0, s>>>(S, active, n_act, acc, jerk, t_new, ldexp(1.0, -lmax),
+                                                          eta, lmin, lmax, st);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t init_levels_launch(const State &S, const double *acc, const double *jerk, double eta_init, int lmin,
+                               int lmax, DevStatus *st, cudaStream_t s, int64_t *launches)
+{
+    init_levels_kernel<<<blocks_for(S.n, kThreads), kThreads, 0, s>>>(S, acc, jerk, eta_init, lmin, lmax, st);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+size_t sched_scratch_bytes(int64_t n)
+{
+    const SchedGeom g = sched_geom(n);
+    return static_cast<size_t>(g.blocks) * (sizeof(unsigned long long) + sizeof(long long));
+}
+
+cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut *out, void *scratch,
+                            cudaStream_t s, int64_t *launches)
+{
+    const SchedGeom g = sched_geom(S.n);
+    unsigned long long *bmin = static_cast<unsigned long long *>(scratch);
+    long long *bcnt = reinterpret_cast<long long *>(bmin + g.blocks);
+    sched_min_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, bmin);
+    sched_count_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, g.blocks, bmin, bcnt, out);
+    sched_write_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, g.blocks, bcnt, out, active);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t energy_launch(const State &S, double eps2, double *phi, double *out, cudaStream_t s,
+                          int64_t *launches)
+{
+    phi_kernel<<<blocks_for(S.n, kETile), kETile, 0, s>>>(S, eps2, phi);
+    energy_sum_kernel<<<1, 1024, 0, s>>>(S, phi, out);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t time_range_launch(const State &S, unsigned long long *out, cudaStream_t s, int64_t *launches)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0xff, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out + 1, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    time_range_kernel<<<blocks_for(S.n, kThreads, 152 * 8), kThreads, 0, s>>>(S, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t aos_to_soa_launch(const double *aos, double *c0, double *c1, double *c2, int64_t n, cudaStream_t s,
+                              int64_t *launches)
+{
+    aos_to_soa_kernel<<<blocks_for(n, kThreads, 152 * 32), kThreads, 0, s>>>(aos, c0, c1, c2, n);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t soa_to_aos_launch(const double *c0, const double *c1, const double *c2, double *aos, int64_t n,
+                              cudaStream_t s, int64_t *launches)
+{
+    soa_to_aos_kernel<<<blocks_for(n, kThreads, 152 * 32), kThreads, 0, s>>>(c0, c1, c2, aos, n);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace nb

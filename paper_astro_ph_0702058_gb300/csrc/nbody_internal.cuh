@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libnbody.so.
+// Not part of the public ABI (that is include/nbody.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "nbody.h"
+
+namespace nb {
+
+// j-particles per shared-memory tile; the j-stream is padded with massless
+// particles at the origin to a multiple of this, and j-ranges of the split
+// force kernel start on tile boundaries.
+constexpr int kJTile = 256;
+constexpr int kModePlain = NBODY_MODE_PLAIN;
+constexpr int kModeComp = NBODY_MODE_COMP;
+
+// Device-side status word of a context (written by kernels, read by the host).
+enum : unsigned {
+    kFlagNonfinite = 1u,
+    kFlagDtMin = 2u,
+    kFlagTimeout = 4u,
+    kFlagBadIndex = 8u,
+};
+
+struct DevStatus {
+    unsigned int flags;
+    int bad_index;
+    unsigned long long below_min;
+    unsigned long long nonfinite;
+};
+
+// FP64 master state, structure of arrays: component c of particle i is x[c][i].
+struct State {
+    int64_t n;
+    const double *m;
+    double *x[3];
+    double *v[3];
+    double *a[3];
+    double *k[3];
+    int64_t *t;     // ticks of dt_min = 2^-lmax
+    int8_t *level;  // dt = 2^-level
+};
+
+// Predicted j-stream read by the force kernel (n_pad entries each).
+struct JStream {
+    float4 *posm;   // (x_hi, y_hi, z_hi, m)
+    float4 *vel;    // (vx, vy, vz, 0)
+    float4 *poslo;  // (x - x_hi, y - y_hi, z - z_hi, 0) rounded to float; compensated mode
+    int64_t n_pad;
+};
+
+struct ForceConfig {
+    int threads;          // threads per block
+    int ipt;              // i-particles per thread
+    int split;            // j-ranges (gridDim.y)
+    int tiles_per_split;  // tiles of kJTile j per range
+    int n_iblk;           // i-blocks (gridDim.x)
+};
+
+// ---- force.cu ----
+extern int g_skip_first_copy;  // test hook: force kernels leave out their first tile copy
+
+// Picks the launch shape for n_act active particles against n_pad j.
+// req_* > 0 override the automatic choice.
+int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_threads,
+                 int req_ipt, int req_split, ForceConfig *cfg);
+// Scratch bytes needed for partial sums when cfg.split > 1 (0 otherwise).
+size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act);
+// Launches the force evaluation (and the fixed-order partial reduction when
+// split > 1).  acc/jerk: n_act*3, pot: n_act, device doubles.
+cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active,
+                         int64_t n_act, float eps2, const ForceConfig &cfg, double *acc,
+                         double *jerk, double *pot, void *partials, DevStatus *st,
+                         cudaStream_t s, int64_t *launches);
+
+// ---- integrator.cu ----
+cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, bool comp,
+                           cudaStream_t s, int64_t *launches);
+cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act,
+                           const double *acc, const double *jerk, int64_t t_new, double eta,
+                           int lmin, int lmax, DevStatus *st, cudaStream_t s, int64_t *launches);
+// a, k <- the full force at t = 0 (acc, jerk: n*3), t <- 0, level from Eq. (initTimestep).
+cudaError_t init_levels_launch(const State &S, const double *acc, const double *jerk,
+                               double eta_init, int lmin, int lmax, DevStatus *st,
+                               cudaStream_t s, int64_t *launches);
+
+struct SchedOut {
+    long long t_blk;
+    long long n_act;
+};
+// Scratch for the scheduler: sched_scratch_bytes(n) bytes of device memory.
+size_t sched_scratch_bytes(int64_t n);
+cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut *out,
+                            void *scratch, cudaStream_t s, int64_t *launches);
+
+// E_kin and E_pot (phi scratch: n doubles; out: 2 doubles).
+cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, double *out,
+                          cudaStream_t s, int64_t *launches);
+// min and max of t over all particles (out: 2 unsigned long long).
+cudaError_t time_range_launch(const State &S, unsigned long long *out, cudaStream_t s,
+                              int64_t *launches);
+
+// a[i] = i for 0 <= i < n.
+cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches);
+
+// Row-major n x 3 <-> three component arrays.
+cudaError_t aos_to_soa_launch(const double *aos, double *c0, double *c1, double *c2, int64_t n,
+                              cudaStream_t s, int64_t *launches);
+cudaError_t soa_to_aos_launch(const double *c0, const double *c1, const double *c2, double *aos,
+                              int64_t n, cudaStream_t s, int64_t *launches);
+
+}  // namespace nb

@@ -1,0 +1,80 @@
+"""The C ABI: the library builds for sm_103a, loads, and exports every call the
+header declares; the binding mirrors them; argument checks that need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nbody.h")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(nbody_[a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_astro_ph_0702058_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_calls():
+    names = header_functions()
+    for required in ("nbody_init", "nbody_predict", "nbody_force", "nbody_correct", "nbody_energy",
+                     "nbody_next_block", "nbody_step", "nbody_get_state", "nbody_set_state", "nbody_free",
+                     "nbody_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_mirrors_header():
+    from paper_astro_ph_0702058_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == header_functions()
+    for name in _lib.EXPORTS:
+        assert callable(getattr(_lib, name)), name
+
+
+def test_strerror_and_argument_checks_without_gpu(libpath):
+    import numpy as np
+
+    from paper_astro_ph_0702058_gb300 import _lib
+    L = _lib.lib()
+    for code in range(-8, 1):
+        assert L.nbody_strerror(code).decode()
+    assert L.nbody_strerror(-99).decode() == "unknown error code"
+    p = _lib.nbody_default_params()
+    assert p.eta == 0.01 and p.lmin == 6 and p.lmax == 26 and p.mode == 0
+    m = np.ones(4)
+    x = np.zeros((4, 3))
+    h = ctypes.c_void_p()
+    # rejected before any device call
+    assert L.nbody_init(ctypes.byref(h), 0, _lib.ptr(m, "f64"), _lib.ptr(x, "f64"), _lib.ptr(x, "f64"), 0.1,
+                        ctypes.byref(p)) == _lib.NBODY_EINVAL
+    assert L.nbody_init(ctypes.byref(h), 4, _lib.ptr(m, "f64"), _lib.ptr(x, "f64"), _lib.ptr(x, "f64"), -1.0,
+                        ctypes.byref(p)) == _lib.NBODY_EINVAL
+    bad = _lib.nbody_default_params()
+    bad.lmin, bad.lmax = 10, 5
+    assert L.nbody_init(ctypes.byref(h), 4, _lib.ptr(m, "f64"), _lib.ptr(x, "f64"), _lib.ptr(x, "f64"), 0.1,
+                        ctypes.byref(bad)) == _lib.NBODY_EINVAL
+    assert "lmin" in _lib.nbody_last_error()
+    assert L.nbody_predict(None, 0.0) == _lib.NBODY_EINVAL
+    L.nbody_free(None)
+
+
+def test_python_binding_rejects_wrong_dtypes():
+    import numpy as np
+
+    from paper_astro_ph_0702058_gb300 import _lib
+    with pytest.raises(TypeError):
+        _lib.ptr(np.zeros(3, dtype=np.float32), "f64")
+    with pytest.raises(ValueError):
+        _lib.ptr(np.zeros((3, 3))[:, 0], "f64")
