@@ -349,6 +349,22 @@ def bench_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def force_only(args):
+    """One nbody_force on all N particles per mode, untimed: the launch that profilers capture."""
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import plummer_sphere
+    m, x, v = plummer_sphere(args.n, SEED)
+    act = torch.arange(args.n, dtype=torch.int32, device="cuda")
+    for mode in args.modes.split(","):
+        with Simulation(m, x, v, EPS2, mode=mode) as sim:
+            sim.predict(0.0)
+            sim.force(act, args.n)
+            sim.sync()
+    print(json.dumps({"force_only": args.n, "modes": args.modes}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +373,13 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="particles (default 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--force-only", action="store_true",
+                    help="run one force call per mode on all N particles (for profilers), no timing")
+    ap.add_argument("--modes", default="plain,comp")
     args = ap.parse_args(argv)
+    if args.force_only:
+        force_only(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     out = bench_reference(args) if args.impl == "reference" else bench_ours(args)

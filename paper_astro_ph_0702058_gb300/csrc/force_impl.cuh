@@ -27,7 +27,18 @@
 #include "nbody_internal.cuh"
 #include "ptx.cuh"
 
+// Compile-time tuning of the tile loop: unroll factor of the j loop and the
+// number of pairs summed in FP32 before each fold into the running total.
+#ifndef NB_JUNROLL
+#define NB_JUNROLL 8
+#endif
+#ifndef NB_FOLD
+#define NB_FOLD 64
+#endif
+
 namespace nb {
+
+constexpr int kJUnroll = NB_JUNROLL;
 
 struct ForceParams {
     const float4 *__restrict__ posm;
@@ -111,7 +122,7 @@ __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, co
         for (int u = 0; u < IPT; ++u)
 #pragma unroll
             for (int c = 0; c < 7; ++c) p[u][c] = 0.0f;
-#pragma unroll 8
+#pragma unroll kJUnroll
         for (int jj = 0; jj < PF; ++jj) {
             const float4 pj = sp[jb + jj];
             const float4 vj = sv[jb + jj];
@@ -329,7 +340,7 @@ __global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int 
 // Fold length (pairs per FP32 partial) of each mode.
 template <int MODE>
 struct FoldLen {
-    static constexpr int value = 64;
+    static constexpr int value = NB_FOLD;
 };
 
 template <int MODE, int NT, int IPT>

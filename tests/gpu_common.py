@@ -7,18 +7,19 @@ from tests.fp32_bounds import bounds
 EPS2 = (1.0 / 256) ** 2
 
 # Tolerances against the FP64 oracle (derivation in DESIGN.md, "Tolerances"):
-#  - every row: |error| <= the a-priori FP32 bound of tests/fp32_bounds.py
-#    (position/velocity rounding, pair arithmetic, summation);
-#  - the per-particle relative thresholds REL (plain: the stated 1e-5;
-#    compensated: 1e-6, since the literal 1e-10 lies below the rounding of one
-#    FP32 pair term) must hold for at least FRAC of the rows when >= 100 rows
-#    are compared.  Acc and pot meet them for 99 % of rows; the jerk, dominated
-#    by the nearest neighbours, carries FP32 position rounding u|x|/r (plain)
-#    and the MUFU rsqrt error five times over (both modes), so a few per cent of
-#    rows exceed the threshold while staying inside their FP32 bound.
+#  - every row, acc and jerk as vectors and pot: |error| <= the a-priori FP32
+#    bound of tests/fp32_bounds.py (position/velocity rounding, pair arithmetic,
+#    summation);
+#  - the stated per-particle relative thresholds on |acc|, |jerk| and pot
+#    (REL: plain 1e-5 as stated; compensated 1e-6, since the literal 1e-10 lies
+#    below the rounding of one FP32 pair term) must hold for at least FRAC of
+#    the rows when >= 100 rows are compared.  In plain mode a few per cent of
+#    rows with a close neighbour exceed 1e-5 on |jerk| (and rarely on |acc|):
+#    FP32 positions carry a relative separation error u|x|/r.  They stay
+#    inside their FP32 bound.
 REL = {"plain": 1e-5, "comp": 1e-6}
-FRAC = {"plain": {"acc": 0.99, "pot": 0.99, "jerk": 0.90, "jerk_mag": 0.90},
-        "comp": {"acc": 0.99, "pot": 0.99, "jerk": 0.95, "jerk_mag": 0.95}}
+FRAC = {"plain": 0.97, "comp": 0.99}
+LITERAL = ("acc_mag", "jerk_mag", "pot")
 
 
 def need_gpu():
@@ -47,8 +48,8 @@ def rel_scalar(got, ref):
 
 
 def errors(acc, jerk, pot, ra, rk, rp):
-    return {"acc": rel_vec(acc, ra), "jerk": rel_vec(jerk, rk), "jerk_mag": rel_mag(jerk, rk),
-            "pot": rel_scalar(pot, rp)}
+    return {"acc": rel_vec(acc, ra), "acc_mag": rel_mag(acc, ra), "jerk": rel_vec(jerk, rk),
+            "jerk_mag": rel_mag(jerk, rk), "pot": rel_scalar(pot, rp)}
 
 
 def check_force(mode, m, x, v, eps2, rows, got, ref, what="", min_rows=100):
@@ -62,9 +63,9 @@ def check_force(mode, m, x, v, eps2, rows, got, ref, what="", min_rows=100):
     assert np.all(worst <= 1.0), f"{what} {mode}: error over the FP32 bound, max err/bound {worst}"
     e = errors(acc, jerk, pot, ra, rk, rp)
     if len(rows) >= min_rows:
-        for key, val in e.items():
-            frac = float(np.mean(val <= REL[mode]))
-            assert frac >= FRAC[mode][key], f"{what} {mode} {key}: only {frac:.3f} of rows within {REL[mode]:.0e}"
+        for key in LITERAL:
+            frac = float(np.mean(e[key] <= REL[mode]))
+            assert frac >= FRAC[mode], f"{what} {mode} {key}: only {frac:.3f} of rows within {REL[mode]:.0e}"
     return e
 
 
