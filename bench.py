@@ -181,13 +181,36 @@ def run_steps(sim, n, steps, warmup, stream, flush, host=None):
     return total, [a.elapsed_time(b) for a, b in force_ms], launches
 
 
-def roofline(force_ms_avg, n, sm_count, clocks, peaks):
+KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_astro_ph_0702058_gb300/csrc/ptx.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic_n1048576.json")
+
+
+def measured_traffic(mode, n):
+    """DRAM bytes per force launch from the committed ncu capture, or None when that
+    capture was of another size or the kernel source has changed since."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if rec.get("source_sha256") != h.hexdigest() or rec.get("n") != n or mode not in rec:
+        return None
+    return rec[mode]["dram_read_bytes"] + rec[mode]["dram_write_bytes"]
+
+
+def roofline(force_ms_avg, n, sm_count, clocks, peaks, mode="comp"):
     max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     pairs = n * (n - 1)
     achieved = pairs / (force_ms_avg * 1e-3) / 1e9
     peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / OPS_PER_PAIR / 1e9
     out = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Gpair/s",
-           "frac": round(achieved / peak, 4), "traffic": None,
+           "frac": round(achieved / peak, 4), "traffic": measured_traffic(mode, n),
+           "traffic_unit": "bytes per launch (ncu dram read + write)",
            "peak_basis": f"{sm_count} SM x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz / "
                          f"{OPS_PER_PAIR} FP32 ops per pair (derived from unit counts and the max SM clock)"}
     if clocks.get("sm_mhz"):
@@ -270,8 +293,8 @@ def bench_ours(args):
     if rank == 0:
         c = res["comp"]
         p = res["plain"]
-        rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks)
-        rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks)
+        rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks, "comp")
+        rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks, "plain")
         out = {
             "metric": METRIC, "value": c["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": c["ms_per_step"], "higher_is_better": True,

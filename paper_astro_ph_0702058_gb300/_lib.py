@@ -244,3 +244,4 @@ def nbody_debug_fail_alloc(k: int) -> None:
 
 def nbody_debug_skip_tile_copy(on: bool) -> None:
     lib().nbody_debug_skip_tile_copy(1 if on else 0)
+

@@ -70,6 +70,12 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
+int nb::report_error(int code, const char *msg)
+{
+    std::snprintf(g_err, sizeof g_err, "%s", msg);
+    return code;
+}
+
 struct nbody_ctx {
     int64_t n = 0, n_pad = 0;
     double eps2 = 0.0;
@@ -360,6 +366,7 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     cudaStream_t s = c->s;
     int64_t *L = &c->stats.kernel_launches;
     NB_INIT(cudaMemsetAsync(c->jbuf, 0, 3 * static_cast<size_t>(c->n_pad) * sizeof(float4), s), "memset");
+    NB_INIT(pad_jstream_launch(c->J, n, s, &c->stats.kernel_launches), "padding kernel");
     NB_INIT(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s), "memset");
     NB_INIT(cudaMemsetAsync(c->state + 7 * nd, 0, 6 * nd * sizeof(double), s), "memset");
     NB_INIT(cudaMemsetAsync(c->t, 0, nd * sizeof(int64_t), s), "memset");

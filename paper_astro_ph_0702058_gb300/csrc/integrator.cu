@@ -407,6 +407,18 @@ __global__ void soa_to_aos_kernel(const double *c0, const double *c1, const doub
     }
 }
 
+// Padding of the j-stream: massless particles far away (r^2 ~ 3e30), so a
+// padding pair adds exactly zero even with eps = 0 and a particle at the origin.
+__global__ void pad_jstream_kernel(float4 *posm, float4 *vel, float4 *poslo, int64_t n, int64_t n_pad)
+{
+    for (int64_t i = n + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_pad;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        posm[i] = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.f);
+        vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        poslo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 __global__ void iota_kernel(int32_t *a, int64_t n)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -415,6 +427,14 @@ __global__ void iota_kernel(int32_t *a, int64_t n)
 }
 
 }  // namespace
+
+cudaError_t pad_jstream_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches)
+{
+    if (J.n_pad <= n) return cudaSuccess;
+    pad_jstream_kernel<<<1, kThreads, 0, s>>>(J.posm, J.vel, J.poslo, n, J.n_pad);
+    ++*launches;
+    return cudaGetLastError();
+}
 
 cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches)
 {

@@ -10,10 +10,14 @@
 
 namespace nb {
 
+// Records the message that nbody_last_error() returns in this thread; returns code.
+int report_error(int code, const char *msg);
+
 // j-particles per shared-memory tile; the j-stream is padded with massless
 // particles at the origin to a multiple of this, and j-ranges of the split
 // force kernel start on tile boundaries.
 constexpr int kJTile = 256;
+constexpr float kPadPosition = 1e15f;  // coordinate of the massless padding particles
 constexpr int kModePlain = NBODY_MODE_PLAIN;
 constexpr int kModeComp = NBODY_MODE_COMP;
 
@@ -45,6 +49,7 @@ struct State {
 };
 
 // Predicted j-stream read by the force kernel (n_pad entries each).
+// Entries n .. n_pad-1 are massless padding far from every particle.
 struct JStream {
     float4 *posm;   // (x_hi, y_hi, z_hi, m)
     float4 *vel;    // (vx, vy, vz, 0)
@@ -103,6 +108,8 @@ cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, doub
 cudaError_t time_range_launch(const State &S, unsigned long long *out, cudaStream_t s,
                               int64_t *launches);
 
+// Fills j-stream entries n .. n_pad-1 with massless particles at kPadPosition.
+cudaError_t pad_jstream_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches);
 // a[i] = i for 0 <= i < n.
 cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches);
 

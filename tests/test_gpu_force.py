@@ -90,6 +90,14 @@ def test_force_zero_softening(torch, mode):
         sim.predict(0.0)
         got = gpu_force(sim, np.arange(300))
     check_force(mode, m, x, v, 0.0, np.arange(300), got, oracle.force(m, x, v, 0.0), "eps0 cluster")
+    # a particle exactly at the origin, with padding entries in the last tile (300 -> 512)
+    x = x.copy()
+    x[0] = 0.0
+    with _sim(m, x, v, 0.0, mode) as sim:
+        sim.predict(0.0)
+        got = gpu_force(sim, np.arange(300))
+    assert np.all(np.isfinite(got[0])) and np.all(np.isfinite(got[2]))
+    check_force(mode, m, x, v, 0.0, np.arange(300), got, oracle.force(m, x, v, 0.0), "particle at origin")
 
 
 @pytest.mark.parametrize("mode", ["plain", "comp"])
