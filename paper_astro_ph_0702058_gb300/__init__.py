@@ -11,7 +11,7 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBodyError,  # noqa: F401
                    nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_default_params, nbody_energy,
-                   nbody_force, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
+                   nbody_force, nbody_force_noalloc, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
                    nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
                    nbody_strerror, nbody_sync)
 

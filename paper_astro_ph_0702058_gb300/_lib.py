@@ -36,7 +36,7 @@ NBODY_MODE_COMP = 1
 EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",
            "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state",
            "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
-           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy")
+           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_force_noalloc")
 
 
 class nbody_params(C.Structure):
@@ -96,6 +96,8 @@ def lib():
             L.nbody_debug_fail_alloc.restype = None
             L.nbody_debug_skip_tile_copy.argtypes = [C.c_int]
             L.nbody_debug_skip_tile_copy.restype = None
+            L.nbody_force_noalloc.argtypes = [P, P, P, C.c_int64, P, C.c_int64, C.c_double, C.c_int, P, P, P, P]
+            L.nbody_force_noalloc.restype = C.c_int
             for name in ("nbody_init", "nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct",
                          "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state", "nbody_set_state",
                          "nbody_get_predicted", "nbody_get_stats"):
@@ -245,3 +247,14 @@ def nbody_debug_fail_alloc(k: int) -> None:
 def nbody_debug_skip_tile_copy(on: bool) -> None:
     lib().nbody_debug_skip_tile_copy(1 if on else 0)
 
+
+def nbody_force_noalloc(posm, vel, poslo, n: int, active, n_act: int, eps2: float, mode: int,
+                        acc, jerk, pot, stream=None) -> None:
+    """Force on a list from the caller's own device j-stream, with no device allocation."""
+    n_pad = (int(n) + 255) // 256 * 256
+    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().nbody_force_noalloc(_ptr_f32(posm, 4 * n_pad), _ptr_f32(vel, 4 * n_pad),
+                                     _ptr_f32(poslo, 4 * n_pad), int(n), ptr(active, "i32", n_act),
+                                     int(n_act), float(eps2), int(mode), ptr(acc, "f64", 3 * n_act),
+                                     ptr(jerk, "f64", 3 * n_act), ptr(pot, "f64", n_act), st),
+           "nbody_force_noalloc")
