@@ -49,8 +49,14 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     const int n_tiles = static_cast<int>(n_pad / kJTile);
     int threads = req_threads;
     int ipt = req_ipt;
+    // Large blocks: 4 i per thread amortise the shared-memory loads over more
+    // pairs (measured 6 % faster than 2 at N = 2^20); small blocks need more
+    // blocks of fewer rows to fill the GPU.
     if (threads == 0) threads = n_act >= 8192 ? 128 : 64;
-    if (ipt == 0) ipt = n_act >= static_cast<int64_t>(sm_count) * 128 * 2 * 2 ? 2 : 1;
+    if (ipt == 0) {
+        const int64_t per_wave = static_cast<int64_t>(sm_count) * 128 * 2;
+        ipt = n_act >= 4 * per_wave ? 4 : n_act >= 2 * per_wave ? 2 : 1;
+    }
     if (shape_index(threads, ipt) < 0) return NBODY_EINVAL;
     const int per = threads * ipt;
     const int n_iblk = static_cast<int>(std::max<int64_t>(1, (n_act + per - 1) / per));

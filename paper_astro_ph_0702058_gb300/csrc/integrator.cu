@@ -6,6 +6,7 @@
 #include <cfloat>
 
 #include "nbody_internal.cuh"
+#include "step_impl.cuh"
 
 namespace nb {
 
@@ -18,17 +19,6 @@ int blocks_for(int64_t n, int threads, int cap = 1 << 20)
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
     return static_cast<int>(b < cap ? b : cap);
-}
-
-// Predictor of Sect. 2 for one component, in Horner form with explicit
-// roundings so that the predictor and the corrector kernels give the same
-// bits:  x_p = x + dt (v + dt (a/2 + dt k/6)),  v_p = v + dt (a + dt k/2).
-__device__ __forceinline__ void predict_dim(double x, double v, double a, double k, double dt,
-                                            double &xp, double &vp)
-{
-    const double k6 = __dmul_rn(k, 1.0 / 6.0);
-    xp = __fma_rn(dt, __fma_rn(dt, __fma_rn(dt, k6, 0.5 * a), v), x);
-    vp = __fma_rn(dt, __fma_rn(dt, 0.5 * k, a), v);
 }
 
 __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int comp)
@@ -51,33 +41,6 @@ __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, do
     }
 }
 
-__device__ __forceinline__ double norm3(const double *u)
-{
-    return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-}
-
-// Level L of the largest power of two 2^-L <= dt, clamped to [lmin, lmax];
-// returns -1 for NaN.  *clamped is set when dt < 2^-lmax (incl. dt <= 0).
-__device__ __forceinline__ int level_of(double dt, int lmin, int lmax, bool *clamped)
-{
-    *clamped = false;
-    if (isnan(dt)) return -1;
-    if (!(dt > 0.0)) {
-        *clamped = true;
-        return lmax;
-    }
-    if (isinf(dt)) return lmin;
-    int e;
-    frexp(dt, &e);  // dt = f 2^e with 1/2 <= f < 1, so 2^(e-1) <= dt < 2^e
-    int L = 1 - e;
-    if (L < lmin) L = lmin;
-    if (L > lmax) {
-        L = lmax;
-        *clamped = true;
-    }
-    return L;
-}
-
 // Corrector of Sect. 2 plus Eq. (timestep), one block row per thread.
 __global__ void correct_kernel(const State S, const int32_t *__restrict__ active, int64_t n_act,
                                const double *__restrict__ acc, const double *__restrict__ jerk,
@@ -92,59 +55,7 @@ __global__ void correct_kernel(const State S, const int32_t *__restrict__ active
         st->bad_index = static_cast<int>(q);
         return;
     }
-    const double dt = static_cast<double>(t_new - S.t[i]) * tick;
-    const double idt = 1.0 / dt;
-    const double idt2 = idt * idt;
-    const double dt3 = dt * dt * dt;
-    const double dt4 = dt3 * dt;
-    double ap[3], kp[3], a2e[3], a3[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double a = S.a[c][i];
-        const double k = S.k[c][i];
-        double xp, vp;
-        predict_dim(S.x[c][i], S.v[c][i], a, k, dt, xp, vp);
-        ap[c] = acc[3 * q + c];
-        kp[c] = jerk[3 * q + c];
-        const double da = a - ap[c];  // Delta a = a - a_p
-        const double a2 = -6.0 * da * idt2 - (4.0 * k + 2.0 * kp[c]) * idt;
-        a3[c] = 12.0 * da * idt2 * idt + 6.0 * (k + kp[c]) * idt2;
-        const double xn = xp + dt4 * (a2 / 24.0 + a3[c] * dt / 120.0);
-        const double vn = vp + dt3 * (a2 / 6.0 + a3[c] * dt / 24.0);
-        a2e[c] = a2 + a3[c] * dt;  // a^(2) at the end of the step
-        finite = finite && isfinite(xn) && isfinite(vn) && isfinite(ap[c]) && isfinite(kp[c]);
-        S.x[c][i] = xn;
-        S.v[c][i] = vn;
-        S.a[c][i] = ap[c];
-        S.k[c][i] = kp[c];
-    }
-    // Eq. (timestep) with end-of-step quantities.
-    const double an = norm3(ap), kn = norm3(kp), a2n = norm3(a2e), a3n = norm3(a3);
-    const double num = an * a2n + kn * kn;
-    const double den = kn * a3n + a2n * a2n;
-    const double dtc = den == 0.0 ? static_cast<double>(INFINITY) : sqrt(eta * num / den);
-    bool clamped = false;
-    const int lc = level_of(dtc, lmin, lmax, &clamped);
-    const int l_old = S.level[i];
-    int l_new;
-    if (!finite || lc < 0) {
-        l_new = lmax;
-        atomicOr(&st->flags, kFlagNonfinite);
-        atomicAdd(&st->nonfinite, 1ull);
-    } else if (lc >= l_old) {
-        l_new = lc;  // shrink at once (or keep)
-    } else {
-        // grow one level, only if the new time is a multiple of twice the old step
-        const int64_t two_old = int64_t(2) << (lmax - l_old);
-        l_new = (l_old - 1 >= lmin && t_new % two_old == 0) ? l_old - 1 : l_old;
-    }
-    if (clamped) {
-        atomicOr(&st->flags, kFlagDtMin);
-        atomicAdd(&st->below_min, 1ull);
-    }
-    S.t[i] = t_new;
-    S.level[i] = static_cast<int8_t>(l_new);
+    correct_row(S, i, acc + 3 * q, jerk + 3 * q, t_new, tick, eta, lmin, lmax, st);
 }
 
 // Start of a run: a, k from the full force at t = 0, t = 0 and the first level
@@ -206,38 +117,6 @@ __device__ __forceinline__ unsigned long long due_tick(const State &S, int64_t i
 {
     return static_cast<unsigned long long>(S.t[i] + (int64_t(1) << (lmax - S.level[i])));
 }
-
-// Block-wide reduction; `id` is the identity of `op` (pads missing warps).
-template <typename T, typename Op>
-__device__ __forceinline__ T block_reduce(T v, Op op, T *sh, T id)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    v = static_cast<int>(threadIdx.x) < nw ? sh[threadIdx.x] : id;
-    if (w == 0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (l == 0) sh[0] = v;
-    }
-    __syncthreads();
-    v = sh[0];
-    __syncthreads();
-    return v;
-}
-
-struct MinOp {
-    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
-};
-struct MaxOp {
-    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; }
-};
-struct SumOp {
-    __device__ long long operator()(long long a, long long b) const { return a + b; }
-};
 
 __global__ void sched_min_kernel(const State S, int lmax, int64_t chunk, unsigned long long *bmin)
 {
