@@ -181,7 +181,8 @@ def run_steps(sim, n, steps, warmup, stream, flush, host=None):
     return total, [a.elapsed_time(b) for a, b in force_ms], launches
 
 
-KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_astro_ph_0702058_gb300/csrc/ptx.cuh")
+KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_astro_ph_0702058_gb300/csrc/ptx.cuh",
+                  "paper_astro_ph_0702058_gb300/csrc/force.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic_n1048576.json")
 
 
