@@ -389,6 +389,58 @@ def force_only(args):
     print(json.dumps({"force_only": args.n, "modes": args.modes}))
 
 
+def ensemble_workload(args):
+    """C4: 512 independent Plummer clusters (sizes log-uniform in [256, 8192) from seed 4),
+    eps = 1/256, eta = 0.02, integrated to t = 1/4 as one batched, graph-replayed run
+    (tuned launch shape), against one context per cluster on a systematic sample."""
+    import numpy as np
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import Ensemble, Simulation
+    from synthetic import ensemble_sizes, plummer_sphere
+    n_cl, t_end, eps2, mode = args.clusters, 0.25, (1.0 / 256) ** 2, args.ens_mode
+    sizes = ensemble_sizes(n_cl, 4)
+    parts = [plummer_sphere(int(n), 4_000_000 + c) for c, n in enumerate(sizes)]
+    m = np.concatenate([p[0] for p in parts])
+    x = np.concatenate([p[1] for p in parts])
+    v = np.concatenate([p[2] for p in parts])
+    torch.cuda.set_device(0)
+    with Ensemble(sizes, m, x, v, eps2, eta=0.02, mode=mode) as ens:
+        ek0, ep0 = ens.energy()
+        e0 = ek0 + ep0
+        shape = ens.tune(t_end, steps=4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = ens.run(t_end)
+        wall = time.perf_counter() - t0
+        st = ens.stats()
+        ek, ep = ens.energy()
+    pairs = int(st["pairs"].sum())
+    # one context per cluster, each run by its own host loop (one launch sequence per block)
+    sample = list(range(0, n_cl, max(1, n_cl // args.ens_sample)))
+    t0 = time.perf_counter()
+    single_pairs = 0
+    for c in sample:
+        mc, xc, vc = parts[c]
+        with Simulation(mc, xc, vc, eps2, eta=0.02, mode=mode) as sim:
+            sim.step(t_end)
+            single_pairs += sim.stats()["pairs"] - len(mc) * (len(mc) - 1)  # without the t = 0 force
+    single = time.perf_counter() - t0
+    per_cluster_s = single / len(sample)
+    out = {"workload": "ensemble", "clusters": n_cl, "particles": int(sizes.sum()), "mode": mode,
+           "t_end": t_end, "batched_steps": int(steps), "blocks_total": int(st["blocks"].sum()),
+           "wall_s": wall, "clusters_per_s": n_cl / wall, "pairs": pairs, "pairs_per_s": pairs / wall,
+           "tuned_shape": {"threads": shape[0], "i_block": shape[1], "tiles_per_range": shape[2],
+                           "ms_per_batched_step_in_tuning": shape[3]},
+           "one_context_per_cluster": {"sample": len(sample), "s_per_cluster": per_cluster_s,
+                                       "clusters_per_s": 1.0 / per_cluster_s,
+                                       "pairs_per_s": single_pairs / single},
+           "speedup_clusters_per_s": (n_cl / wall) * per_cluster_s,
+           "energy_error_median": float(np.median(np.abs((ek + ep - e0) / e0))),
+           "energy_error_max": float(np.max(np.abs((ek + ep - e0) / e0)))}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,9 +452,17 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
+    ap.add_argument("--workload", choices=["c3", "ensemble"], default="c3",
+                    help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run")
+    ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--ens-sample", type=int, default=32, help="clusters run one context each, for comparison")
+    ap.add_argument("--ens-mode", default="comp")
     args = ap.parse_args(argv)
     if args.force_only:
         force_only(args)
+        return
+    if args.workload == "ensemble":
+        ensemble_workload(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -219,6 +219,67 @@ void nbody_debug_fail_alloc(int k);
  * the context stays usable.  Exercises the failure path of the device waits. */
 void nbody_debug_skip_tile_copy(int on);
 
+/* ---------------------------------------------------------------- ensembles
+ * Many independent clusters integrated together: each cluster runs the block-
+ * step scheme of Sect. 2 with its own schedule (its own t_blk and block), and
+ * one batched step advances every unfinished cluster by one of its block
+ * steps.  The batched step is five kernels sized from device-side counts (a
+ * scheduler per cluster, a planner, the predictor, a persistent force kernel
+ * working through a list of (cluster, i-block, j-range) items, the corrector),
+ * so nbody_ens_run captures it once in a CUDA graph and replays it without a
+ * host synchronisation per step. */
+typedef struct nbody_ens nbody_ens; /* opaque; owns all of its device memory */
+
+/* Creates an ensemble of n_clusters clusters on the current device.  sizes
+ * [n_clusters] (host or device) gives each cluster's particle count (>= 1);
+ * m, x, v hold all clusters' particles one after the other (cluster 0 first),
+ * in the layout of nbody_init.  Every cluster starts at t = 0 with its full
+ * force and first levels (Eq. initTimestep).  p as for nbody_init (j_tile,
+ * i_block, j_split are ignored; see nbody_ens_set_shape).  The ensemble runs
+ * on p->stream or, if that is NULL, on a stream of its own.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENONFINITE. */
+int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, const double *m,
+                   const double *x, const double *v, double eps2, const nbody_params *p);
+
+/* Force launch shape: threads per block (64 or 128), i-particles per thread
+ * (1 or 2), and j-tiles of 256 particles per work item (>= 1; each cluster is
+ * cut into at most 8 j-ranges).  Errors: EINVAL for unsupported shapes. */
+int nbody_ens_set_shape(nbody_ens *e, int threads, int i_block, int tiles_per_range);
+
+/* Autotuner: times `steps` batched steps towards t_end for every supported
+ * shape from the current state (restored after each trial), keeps the fastest
+ * and returns it (any output may be NULL); best_ms is its time per batched
+ * step.  The ensemble's state is unchanged. */
+int nbody_ens_tune(nbody_ens *e, double t_end, int steps, int *threads, int *i_block,
+                   int *tiles_per_range, double *best_ms);
+
+/* One batched step towards t_end (a multiple of dt_max), without a graph;
+ * *n_live receives the number of clusters that took a block step.  Waits. */
+int nbody_ens_step(nbody_ens *e, double t_end, int64_t *n_live);
+
+/* Batched steps through a CUDA graph until every cluster has reached t_end
+ * (a multiple of dt_max); the host checks completion every check_every graph
+ * launches (<= 0: 16).  *n_steps (may be NULL) receives the batched steps
+ * that did work.  Waits.  The first call, and every call after a change of
+ * t_end or shape, captures the graph on the ensemble's stream. */
+int nbody_ens_run(nbody_ens *e, double t_end, int64_t check_every, int64_t *n_steps);
+
+/* Per-cluster E_kin, E_pot (n_clusters each, host) at a time when every
+ * particle of each cluster is at that cluster's common time; else ENOTSYNC. */
+int nbody_ens_energy(nbody_ens *e, double *ekin, double *epot);
+
+/* State of all particles in the layout of nbody_get_state (any may be NULL). */
+int nbody_ens_get_state(nbody_ens *e, double *x, double *v, double *a, double *k,
+                        int64_t *t_tick, int8_t *level);
+
+/* Block steps taken and pair interactions (sum of n_act (N_c - 1) over its
+ * blocks) evaluated per cluster since nbody_ens_init (n_clusters each, host;
+ * may be NULL), and the number of kernels the ensemble has launched. */
+int nbody_ens_get_stats(nbody_ens *e, int64_t *blocks_per_cluster, int64_t *pairs_per_cluster,
+                        int64_t *kernel_launches);
+
+void nbody_ens_free(nbody_ens *e);
+
 /* Force on a list without any device allocation.  The paper has no
  * counterpart: this call serves callers that cannot allocate device memory
  * while they run (a host application that owns all GPU memory through its

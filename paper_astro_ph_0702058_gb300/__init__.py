@@ -10,6 +10,8 @@ from __future__ import annotations
 
 from . import _lib
 from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBodyError,  # noqa: F401
+                   nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
+                   nbody_ens_init, nbody_ens_run, nbody_ens_set_shape, nbody_ens_step, nbody_ens_tune,
                    nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_default_params, nbody_energy,
                    nbody_force, nbody_force_noalloc, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
                    nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
@@ -90,6 +92,84 @@ class Simulation:
         if self._ctx is not None:
             nbody_free(self._ctx)
             self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent clusters integrated together (one library ensemble handle).
+
+    ``sizes`` (n_clusters,) particle counts; ``m``, ``x``, ``v`` hold all
+    clusters' particles one after the other.  Other arguments as ``Simulation``.
+    """
+
+    def __init__(self, sizes, m, x, v, eps2, *, eta=0.02, eta_init=None, lmin=6, lmax=26, mode="plain",
+                 strict=False, stream=None):
+        import numpy as np
+        p = nbody_default_params()
+        p.eta = float(eta)
+        p.eta_init = float(eta_init) if eta_init is not None else 0.0
+        p.lmin, p.lmax = int(lmin), int(lmax)
+        p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        p.strict = 1 if strict else 0
+        if stream is not None:
+            p.stream = int(getattr(stream, "cuda_stream", stream))
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        self.n_clusters = int(self.sizes.shape[0])
+        self.n = int(self.sizes.sum())
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        self._h = nbody_ens_init(self.n_clusters, self.sizes, m, x, v, eps2, p)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("ensemble closed")
+        return self._h
+
+    def set_shape(self, threads, i_block, tiles_per_range):
+        nbody_ens_set_shape(self.handle, threads, i_block, tiles_per_range)
+
+    def tune(self, t_end, steps=4):
+        """(threads, i_block, tiles_per_range, ms per batched step) of the fastest shape."""
+        return nbody_ens_tune(self.handle, t_end, steps)
+
+    def step(self, t_end):
+        return nbody_ens_step(self.handle, t_end)
+
+    def run(self, t_end, check_every=16):
+        return nbody_ens_run(self.handle, t_end, check_every)
+
+    def energy(self):
+        import numpy as np
+        ek = np.zeros(self.n_clusters)
+        ep = np.zeros(self.n_clusters)
+        nbody_ens_energy(self.handle, self.n_clusters, ek, ep)
+        return ek, ep
+
+    def get_state(self, x=None, v=None, a=None, k=None, t_tick=None, level=None):
+        nbody_ens_get_state(self.handle, self.n, x, v, a, k, t_tick, level)
+
+    def stats(self):
+        import numpy as np
+        blocks = np.zeros(self.n_clusters, dtype=np.int64)
+        pairs = np.zeros(self.n_clusters, dtype=np.int64)
+        launches = nbody_ens_get_stats(self.handle, self.n_clusters, blocks, pairs)
+        return {"blocks": blocks, "pairs": pairs, "kernel_launches": launches}
+
+    def close(self):
+        if self._h is not None:
+            nbody_ens_free(self._h)
+            self._h = None
 
     def __enter__(self):
         return self

@@ -36,7 +36,9 @@ NBODY_MODE_COMP = 1
 EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",
            "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state",
            "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
-           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_force_noalloc")
+           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_force_noalloc",
+           "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
+           "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_ens_free")
 
 
 class nbody_params(C.Structure):
@@ -98,6 +100,21 @@ def lib():
             L.nbody_debug_skip_tile_copy.restype = None
             L.nbody_force_noalloc.argtypes = [P, P, P, C.c_int64, P, C.c_int64, C.c_double, C.c_int, P, P, P, P]
             L.nbody_force_noalloc.restype = C.c_int
+            I = C.POINTER(C.c_int)
+            L.nbody_ens_init.argtypes = [C.POINTER(C.c_void_p), C.c_int64, P, P, P, P, C.c_double,
+                                         C.POINTER(nbody_params)]
+            L.nbody_ens_set_shape.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            L.nbody_ens_tune.argtypes = [P, C.c_double, C.c_int, I, I, I, C.POINTER(C.c_double)]
+            L.nbody_ens_step.argtypes = [P, C.c_double, C.POINTER(C.c_int64)]
+            L.nbody_ens_run.argtypes = [P, C.c_double, C.c_int64, C.POINTER(C.c_int64)]
+            L.nbody_ens_energy.argtypes = [P, P, P]
+            L.nbody_ens_get_state.argtypes = [P, P, P, P, P, P, P]
+            L.nbody_ens_get_stats.argtypes = [P, P, P, C.POINTER(C.c_int64)]
+            L.nbody_ens_free.argtypes = [P]
+            L.nbody_ens_free.restype = None
+            for name in ("nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step",
+                         "nbody_ens_run", "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats"):
+                getattr(L, name).restype = C.c_int
             for name in ("nbody_init", "nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct",
                          "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state", "nbody_set_state",
                          "nbody_get_predicted", "nbody_get_stats"):
@@ -258,3 +275,58 @@ def nbody_force_noalloc(posm, vel, poslo, n: int, active, n_act: int, eps2: floa
                                      int(n_act), float(eps2), int(mode), ptr(acc, "f64", 3 * n_act),
                                      ptr(jerk, "f64", 3 * n_act), ptr(pot, "f64", n_act), st),
            "nbody_force_noalloc")
+
+
+def nbody_ens_init(n_clusters: int, sizes, m, x, v, eps2: float, params: nbody_params):
+    h = C.c_void_p()
+    n = int(sum(int(s) for s in sizes))
+    _check(lib().nbody_ens_init(C.byref(h), int(n_clusters), ptr(sizes, "i64", n_clusters), ptr(m, "f64", n),
+                                ptr(x, "f64", 3 * n), ptr(v, "f64", 3 * n), float(eps2), C.byref(params)),
+           "nbody_ens_init")
+    return h
+
+
+def nbody_ens_set_shape(ens, threads: int, i_block: int, tiles_per_range: int) -> None:
+    _check(lib().nbody_ens_set_shape(ens, int(threads), int(i_block), int(tiles_per_range)), "nbody_ens_set_shape")
+
+
+def nbody_ens_tune(ens, t_end: float, steps: int = 4):
+    t, i, p = C.c_int(), C.c_int(), C.c_int()
+    ms = C.c_double()
+    _check(lib().nbody_ens_tune(ens, float(t_end), int(steps), C.byref(t), C.byref(i), C.byref(p), C.byref(ms)),
+           "nbody_ens_tune")
+    return t.value, i.value, p.value, ms.value
+
+
+def nbody_ens_step(ens, t_end: float) -> int:
+    live = C.c_int64()
+    _check(lib().nbody_ens_step(ens, float(t_end), C.byref(live)), "nbody_ens_step")
+    return live.value
+
+
+def nbody_ens_run(ens, t_end: float, check_every: int = 16) -> int:
+    ns = C.c_int64()
+    _check(lib().nbody_ens_run(ens, float(t_end), int(check_every), C.byref(ns)), "nbody_ens_run")
+    return ns.value
+
+
+def nbody_ens_energy(ens, n_clusters: int, ekin, epot) -> None:
+    _check(lib().nbody_ens_energy(ens, ptr(ekin, "f64", n_clusters), ptr(epot, "f64", n_clusters)),
+           "nbody_ens_energy")
+
+
+def nbody_ens_get_state(ens, n, x=None, v=None, a=None, k=None, t_tick=None, level=None) -> None:
+    _check(lib().nbody_ens_get_state(ens, ptr(x, "f64", 3 * n), ptr(v, "f64", 3 * n), ptr(a, "f64", 3 * n),
+                                     ptr(k, "f64", 3 * n), ptr(t_tick, "i64", n), ptr(level, "i8", n)),
+           "nbody_ens_get_state")
+
+
+def nbody_ens_get_stats(ens, n_clusters: int, blocks=None, pairs=None):
+    kl = C.c_int64()
+    _check(lib().nbody_ens_get_stats(ens, ptr(blocks, "i64", n_clusters), ptr(pairs, "i64", n_clusters),
+                                     C.byref(kl)), "nbody_ens_get_stats")
+    return kl.value
+
+
+def nbody_ens_free(ens) -> None:
+    lib().nbody_ens_free(ens)
