@@ -219,6 +219,23 @@ void nbody_debug_fail_alloc(int k);
  * the context stays usable.  Exercises the failure path of the device waits. */
 void nbody_debug_skip_tile_copy(int on);
 
+/* ------------------------------------------------------------ differentiation
+ * Reverse mode of a shared-step rollout: the force of Eq. (Force) at t = 0,
+ * then `steps` Hermite steps (Sect. 2 predictor and corrector) of one shared
+ * step dt = 2^-level, in the precision `mode` (FP32 pair math, FP64 state).
+ * Loss L = sum_i |x_i|^2 + E_pot at the end, E_pot the softened potential
+ * energy (FP64).  Writes L to *loss and its gradients with respect to the
+ * initial positions, velocities (n x 3) and masses (n) to g_x0, g_v0, g_m
+ * (host or device).  The adjoint transposes the predictor and corrector and
+ * applies a hand-written vector-Jacobian product of the pair force (FP32
+ * pair math, FP64 totals); states are checkpointed every checkpoint_every
+ * steps (<= 0: 16) and each segment is recomputed forward during the
+ * backward sweep.  eps2 must be > 0.  Allocates its own scratch; waits.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENONFINITE. */
+int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const double *v0, double eps2,
+                       int level, int64_t steps, int64_t checkpoint_every, int mode, double *loss,
+                       double *g_x0, double *g_v0, double *g_m, void *stream);
+
 /* ---------------------------------------------------------------- ensembles
  * Many independent clusters integrated together: each cluster runs the block-
  * step scheme of Sect. 2 with its own schedule (its own t_blk and block), and
@@ -234,9 +251,12 @@ typedef struct nbody_ens nbody_ens; /* opaque; owns all of its device memory */
  * [n_clusters] (host or device) gives each cluster's particle count (>= 1);
  * m, x, v hold all clusters' particles one after the other (cluster 0 first),
  * in the layout of nbody_init.  Every cluster starts at t = 0 with its full
- * force and first levels (Eq. initTimestep).  p as for nbody_init (j_tile,
- * i_block, j_split are ignored; see nbody_ens_set_shape).  The ensemble runs
- * on p->stream or, if that is NULL, on a stream of its own.
+ * force and first levels (Eq. initTimestep).  p as for nbody_init, except that
+ * j_tile, i_block and j_split give the ensemble's force shape (threads per
+ * block, i per thread, tiles per j-range; 0 = 64, 1, 4; see
+ * nbody_ens_set_shape).  The ensemble runs on p->stream (which must allow
+ * stream capture: not the legacy default stream) or, if that is NULL, on a
+ * stream of its own.
  * Errors: EINVAL, ENOMEM, ECUDA, ENONFINITE. */
 int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, const double *m,
                    const double *x, const double *v, double eps2, const nbody_params *p);

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 from . import _lib
 from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBodyError,  # noqa: F401
+                   nbody_diff_rollout,
                    nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
                    nbody_ens_init, nbody_ens_run, nbody_ens_set_shape, nbody_ens_step, nbody_ens_tune,
                    nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_default_params, nbody_energy,
@@ -114,9 +115,10 @@ class Ensemble:
     """
 
     def __init__(self, sizes, m, x, v, eps2, *, eta=0.02, eta_init=None, lmin=6, lmax=26, mode="plain",
-                 strict=False, stream=None):
+                 strict=False, stream=None, threads=0, i_block=0, tiles_per_range=0):
         import numpy as np
         p = nbody_default_params()
+        p.j_tile, p.i_block, p.j_split = int(threads), int(i_block), int(tiles_per_range)
         p.eta = float(eta)
         p.eta_init = float(eta_init) if eta_init is not None else 0.0
         p.lmin, p.lmax = int(lmin), int(lmax)

@@ -38,7 +38,8 @@ EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_pred
            "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
            "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_force_noalloc",
            "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
-           "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_ens_free")
+           "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_ens_free",
+           "nbody_diff_rollout")
 
 
 class nbody_params(C.Structure):
@@ -110,6 +111,9 @@ def lib():
             L.nbody_ens_energy.argtypes = [P, P, P]
             L.nbody_ens_get_state.argtypes = [P, P, P, P, P, P, P]
             L.nbody_ens_get_stats.argtypes = [P, P, P, C.POINTER(C.c_int64)]
+            L.nbody_diff_rollout.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int, C.c_int64, C.c_int64, C.c_int,
+                                             P, P, P, P, P]
+            L.nbody_diff_rollout.restype = C.c_int
             L.nbody_ens_free.argtypes = [P]
             L.nbody_ens_free.restype = None
             for name in ("nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step",
@@ -330,3 +334,12 @@ def nbody_ens_get_stats(ens, n_clusters: int, blocks=None, pairs=None):
 
 def nbody_ens_free(ens) -> None:
     lib().nbody_ens_free(ens)
+
+
+def nbody_diff_rollout(n: int, m, x0, v0, eps2: float, level: int, steps: int, checkpoint_every: int, mode: int,
+                       loss, g_x0, g_v0, g_m, stream=None) -> None:
+    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().nbody_diff_rollout(int(n), ptr(m, "f64", n), ptr(x0, "f64", 3 * n), ptr(v0, "f64", 3 * n),
+                                    float(eps2), int(level), int(steps), int(checkpoint_every), int(mode),
+                                    ptr(loss, "f64", 1), ptr(g_x0, "f64", 3 * n), ptr(g_v0, "f64", 3 * n),
+                                    ptr(g_m, "f64", n), st), "nbody_diff_rollout")

@@ -610,6 +610,136 @@ int nbody_get_stats(nbody_ctx *c, nbody_stats *s)
     return NBODY_OK;
 }
 
+int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const double *v0, double eps2, int level,
+                       int64_t steps, int64_t checkpoint_every, int mode, double *loss, double *g_x0,
+                       double *g_v0, double *g_m, void *stream)
+{
+    g_err[0] = '\0';
+    if (!m || !x0 || !v0 || !loss || !g_x0 || !g_v0 || !g_m) return fail(NBODY_EINVAL, "nbody_diff_rollout: null argument");
+    if (!(eps2 > 0.0)) return fail(NBODY_EINVAL, "nbody_diff_rollout: eps2 must be > 0");
+    if (level < 0 || level > 40 || steps < 0) return fail(NBODY_EINVAL, "nbody_diff_rollout: bad level or steps");
+    if (checkpoint_every <= 0) checkpoint_every = 16;
+    nbody_params p;
+    nbody_default_params(&p);
+    p.lmin = p.lmax = level;  // one shared power-of-two step: every block is all particles
+    p.mode = mode;
+    p.stream = stream;
+    nbody_ctx *c = nullptr;
+    int r = nbody_init(&c, n, m, x0, v0, eps2, &p);
+    if (r != NBODY_OK) return r;
+    const size_t nd = static_cast<size_t>(n);
+    const size_t npad = static_cast<size_t>(c->n_pad);
+    const int64_t n_ck = steps / checkpoint_every + 1;
+    const size_t state_doubles = 12 * nd;  // x, v, a, k (contiguous after m)
+    double *ck = nullptr, *seg = nullptr, *gbuf = nullptr, *lval = nullptr, *dloss = nullptr;
+    float4 *g4 = nullptr;
+    DiffGrads G{};
+    const double dt = std::ldexp(1.0, -level);
+    const float e2 = static_cast<float>(eps2);
+    cudaStream_t s = c->s;
+    int64_t *L = &c->stats.kernel_launches;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        void *bufs[] = {ck, seg, gbuf, lval, dloss, g4};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        nbody_free(c);
+        return code;
+    };
+#define NB_DR(call, what)                                     \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return done(cuda_fail(e_, what)); \
+    } while (0)
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&ck), n_ck * state_doubles * sizeof(double)), "checkpoints");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&seg), checkpoint_every * state_doubles * sizeof(double)), "segment");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&gbuf), 19 * nd * sizeof(double)), "gradients");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&lval), nd * sizeof(double)), "loss terms");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&dloss), sizeof(double)), "loss");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&g4), 2 * npad * sizeof(float4)), "force upstream");
+    NB_DR(cudaMemsetAsync(gbuf, 0, 19 * nd * sizeof(double), s), "memset");
+    NB_DR(cudaMemsetAsync(g4, 0, 2 * npad * sizeof(float4), s), "memset");
+    for (int q = 0; q < 3; ++q) {
+        G.gx[q] = gbuf + (0 + q) * nd;
+        G.gv[q] = gbuf + (3 + q) * nd;
+        G.ga[q] = gbuf + (6 + q) * nd;
+        G.gk[q] = gbuf + (9 + q) * nd;
+        G.gxp[q] = gbuf + (12 + q) * nd;
+        G.gvp[q] = gbuf + (15 + q) * nd;
+    }
+    G.gm = gbuf + 18 * nd;
+    G.gA = g4;
+    G.gK = g4 + npad;
+    double *xvak = c->state + nd;  // x[3], v[3], a[3], k[3]
+    NB_DR(iota_launch(c->act_force, n, s, L), "index kernel");
+    // one shared Hermite step from tick s0 to s0 + 1 (all particles in the block)
+    auto step = [&](int64_t s0) -> int {
+        int rr = predict_internal(c, s0 + 1);
+        if (rr != NBODY_OK) return rr;
+        rr = force_internal(c, n);
+        if (rr != NBODY_OK) return rr;
+        return correct_internal(c, c->act_force, n, c->f_acc, c->f_jerk);
+    };
+    auto restore = [&](const double *src, int64_t tick) -> int {
+        NB_CUDA(cudaMemcpyAsync(xvak, src, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "restore");
+        NB_CUDA(set_time_launch(c->S, tick, level, s, L), "time kernel");
+        c->t_max = tick;
+        return NBODY_OK;
+    };
+    // forward with checkpoints
+    NB_DR(cudaMemcpyAsync(ck, xvak, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "checkpoint");
+    for (int64_t k = 0; k < steps; ++k) {
+        r = step(k);
+        if (r != NBODY_OK) return done(r);
+        if ((k + 1) % checkpoint_every == 0)
+            NB_DR(cudaMemcpyAsync(ck + ((k + 1) / checkpoint_every) * state_doubles, xvak,
+                                  state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                  "checkpoint");
+    }
+    NB_DR(loss_launch(c->S, eps2, G, lval, dloss, s, L), "loss kernels");
+    // backward, one checkpoint segment at a time
+    for (int64_t seg0 = (steps - 1) / checkpoint_every * checkpoint_every; steps > 0 && seg0 >= 0;
+         seg0 -= checkpoint_every) {
+        const int64_t seg1 = std::min(seg0 + checkpoint_every, steps);
+        r = restore(ck + (seg0 / checkpoint_every) * state_doubles, seg0);
+        if (r != NBODY_OK) return done(r);
+        for (int64_t k = seg0; k < seg1; ++k) {
+            NB_DR(cudaMemcpyAsync(seg + (k - seg0) * state_doubles, xvak, state_doubles * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, s),
+                  "segment");
+            if (k + 1 < seg1) {
+                r = step(k);
+                if (r != NBODY_OK) return done(r);
+            }
+        }
+        for (int64_t k = seg1 - 1; k >= seg0; --k) {
+            r = restore(seg + (k - seg0) * state_doubles, k);
+            if (r != NBODY_OK) return done(r);
+            r = predict_internal(c, k + 1);  // j-stream at the predicted state of step k
+            if (r != NBODY_OK) return done(r);
+            NB_DR(adj_correct_launch(G, n, dt, s, L), "adjoint corrector");
+            NB_DR(force_vjp_launch(c->J, G, n, e2, s, L), "force adjoint");
+            NB_DR(adj_predict_launch(G, n, dt, s, L), "adjoint predictor");
+        }
+    }
+    // the t = 0 force
+    r = restore(ck, 0);
+    if (r != NBODY_OK) return done(r);
+    r = predict_internal(c, 0);
+    if (r != NBODY_OK) return done(r);
+    NB_DR(adj_init_launch(G, n, s, L), "adjoint init");
+    NB_DR(force_vjp_launch(c->J, G, n, e2, s, L), "force adjoint");
+    NB_DR(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDefault, s), "loss copy");
+    NB_DR(soa_to_aos_launch(G.gxp[0], G.gxp[1], G.gxp[2], c->stage, n, s, L), "layout");
+    NB_DR(cudaMemcpyAsync(g_x0, c->stage, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
+    NB_DR(soa_to_aos_launch(G.gvp[0], G.gvp[1], G.gvp[2], c->stage + 3 * nd, n, s, L), "layout");
+    NB_DR(cudaMemcpyAsync(g_v0, c->stage + 3 * nd, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
+    NB_DR(cudaMemcpyAsync(g_m, G.gm, nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
+    r = sync_and_check(c);
+#undef NB_DR
+    return done(r);
+}
+
 void nbody_free(nbody_ctx *c)
 {
     if (!c) return;

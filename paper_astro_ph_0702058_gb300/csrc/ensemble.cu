@@ -697,8 +697,16 @@ int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, co
     const int64_t n = off.back();
     if (n > 2147483647LL || jt > 2147483647LL) return efail(NBODY_EINVAL, "nbody_ens_init: too many particles");
 
+    const int sh_t = prm.j_tile ? prm.j_tile : 64, sh_i = prm.i_block ? prm.i_block : 1;
+    const int sh_p = prm.j_split > 0 ? prm.j_split : 4;
+    bool shape_ok = false;
+    for (const EnsShape &sh : kEnsShapes) shape_ok |= sh.threads == sh_t && sh.ipt == sh_i;
+    if (!shape_ok) return efail(NBODY_EINVAL, "nbody_ens_init: unsupported force shape %d x %d", sh_t, sh_i);
     nbody_ens *e = new (std::nothrow) nbody_ens;
     if (!e) return efail(NBODY_ENOMEM, "nbody_ens_init: host allocation failed");
+    e->threads = sh_t;
+    e->ipt = sh_i;
+    e->tiles_per_range = sh_p;
     e->n_cl = static_cast<int>(n_clusters);
     e->n_tot = n;
     e->j_tot = jt;

@@ -1,5 +1,5 @@
 // Instantiates the force kernels of the comp mode (see force_impl.cuh).
-#include "force_impl.cuh"
+#include "force_dispatch.cuh"
 
 namespace nb {
 

@@ -1,0 +1,86 @@
+// Launch and dispatch of the force kernels over the compiled launch shapes.
+// NB_PACKED selects the packed-FP32 pair loop (force_x2.cuh) instead of the
+// scalar one (force_impl.cuh) at build time.
+#pragma once
+
+#include "force_impl.cuh"
+#include "force_x2.cuh"
+
+#ifndef NB_PACKED
+#define NB_PACKED 0
+#endif
+
+namespace nb {
+
+template <int MODE, int NT, int IPT>
+cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+    dim3 grid(cfg.n_iblk, cfg.split);
+    if (NB_PACKED)
+        force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
+    else
+        force_kernel<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int MODE, int NT, int IPT>
+int occupancy_instance(int *blocks)
+{
+    if (NB_PACKED)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks, force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value>, NT, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
+                                                         NT, 0);
+}
+
+// Dispatch over the compiled shapes of one mode.
+template <int MODE>
+cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+#define NB_CASE(T, I) \
+    if (cfg.threads == T && cfg.ipt == I) return launch_force_instance<MODE, T, I>(P, cfg, s);
+    NB_CASE(64, 1)
+    NB_CASE(64, 2)
+    NB_CASE(64, 4)
+    NB_CASE(128, 1)
+    NB_CASE(128, 2)
+    NB_CASE(128, 4)
+    NB_CASE(256, 1)
+    NB_CASE(256, 2)
+    NB_CASE(256, 4)
+#undef NB_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+template <int MODE>
+int force_occupancy(int threads, int ipt)
+{
+    int b = 0;
+#define NB_CASE(T, I) \
+    if (threads == T && ipt == I) { occupancy_instance<MODE, T, I>(&b); return b; }
+    NB_CASE(64, 1)
+    NB_CASE(64, 2)
+    NB_CASE(64, 4)
+    NB_CASE(128, 1)
+    NB_CASE(128, 2)
+    NB_CASE(128, 4)
+    NB_CASE(256, 1)
+    NB_CASE(256, 2)
+    NB_CASE(256, 4)
+#undef NB_CASE
+    return 0;
+}
+
+template <int MODE>
+cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, double *jerk,
+                          double *pot, cudaStream_t s)
+{
+    const int nt = 256;
+    if (split >= 32 && n_act <= 8192)
+        reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+    else
+        reduce_partials_kernel<MODE><<<(n_act + nt - 1) / nt, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

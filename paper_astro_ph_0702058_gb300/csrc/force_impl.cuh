@@ -108,6 +108,12 @@ __device__ __forceinline__ void fold_ds(float &hi, float &lo, const float x)
     lo = lo + e;
 }
 
+// Fold length (pairs per FP32 partial) of each mode.
+template <int MODE>
+struct FoldLen {
+    static constexpr int value = NB_FOLD;
+};
+
 // Sums over one staged tile of kJTile j (starting at global index j0).
 template <int MODE, int IPT, int PF, bool SELF>
 __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, const float4 *sl, const int j0,
@@ -335,77 +341,6 @@ __global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int 
         jerk[3 * static_cast<size_t>(q) + 2] = r[5];
         pot[q] = r[6];
     }
-}
-
-// Fold length (pairs per FP32 partial) of each mode.
-template <int MODE>
-struct FoldLen {
-    static constexpr int value = NB_FOLD;
-};
-
-template <int MODE, int NT, int IPT>
-cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
-{
-    dim3 grid(cfg.n_iblk, cfg.split);
-    force_kernel<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
-    return cudaGetLastError();
-}
-
-template <int MODE, int NT, int IPT>
-int occupancy_instance(int *blocks)
-{
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
-                                                         NT, 0);
-}
-
-// Dispatch over the compiled shapes of one mode.
-template <int MODE>
-cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
-{
-#define NB_CASE(T, I) \
-    if (cfg.threads == T && cfg.ipt == I) return launch_force_instance<MODE, T, I>(P, cfg, s);
-    NB_CASE(64, 1)
-    NB_CASE(64, 2)
-    NB_CASE(64, 4)
-    NB_CASE(128, 1)
-    NB_CASE(128, 2)
-    NB_CASE(128, 4)
-    NB_CASE(256, 1)
-    NB_CASE(256, 2)
-    NB_CASE(256, 4)
-#undef NB_CASE
-    return cudaErrorInvalidConfiguration;
-}
-
-template <int MODE>
-int force_occupancy(int threads, int ipt)
-{
-    int b = 0;
-#define NB_CASE(T, I) \
-    if (threads == T && ipt == I) { occupancy_instance<MODE, T, I>(&b); return b; }
-    NB_CASE(64, 1)
-    NB_CASE(64, 2)
-    NB_CASE(64, 4)
-    NB_CASE(128, 1)
-    NB_CASE(128, 2)
-    NB_CASE(128, 4)
-    NB_CASE(256, 1)
-    NB_CASE(256, 2)
-    NB_CASE(256, 4)
-#undef NB_CASE
-    return 0;
-}
-
-template <int MODE>
-cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, double *jerk,
-                          double *pot, cudaStream_t s)
-{
-    const int nt = 256;
-    if (split >= 32 && n_act <= 8192)
-        reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
-    else
-        reduce_partials_kernel<MODE><<<(n_act + nt - 1) / nt, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
-    return cudaGetLastError();
 }
 
 }  // namespace nb

@@ -1,0 +1,310 @@
+// Packed-FP32 (f32x2) form of the force kernel of force_impl.cuh.
+//
+// Blackwell executes `fma/mul/add/sub .f32x2` on two FP32 values per lane
+// in one instruction.  The pair loop issues ~30 instructions per pair in the
+// scalar form and is limited by instruction dispatch, not by the FP32 pipe;
+// here two consecutive j share one packed instruction stream:
+//   - j-tiles arrive as float4 by bulk async copy (double-buffered, as in the
+//     scalar kernel) and are transposed once per tile into structure-of-
+//     arrays shared memory, so one 128-bit shared load yields two packed
+//     (j, j+1) pairs of a component;
+//   - each i-particle is broadcast once into packed registers {x_i, x_i};
+//   - the pair term of Appendix A runs on packed operands, with the MUFU
+//     reciprocal square root applied to each half;
+//   - the two halves hold partial sums of the even and odd j of a fold; they
+//     are added at each 64-pair fold, then folded into the running total as in
+//     the scalar kernel (FP32 add, or TwoSum into double-single).
+#pragma once
+
+#include "force_impl.cuh"
+
+namespace nb {
+
+typedef unsigned long long f2_t;  // two packed floats {lo, hi}
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t r, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+struct I2 {  // one i-particle, broadcast into both halves
+    f2_t x, y, z, vx, vy, vz, lx, ly, lz;
+};
+
+// Two pair terms (j = 2 consecutive particles, one i) on packed operands.
+template <int MODE, bool SELF>
+__device__ __forceinline__ void pair_term_x2(const f2_t X, const f2_t Y, const f2_t Z, const f2_t M,
+                                             const f2_t VX, const f2_t VY, const f2_t VZ, const f2_t LX,
+                                             const f2_t LY, const f2_t LZ, const I2 &I, const f2_t E2,
+                                             const f2_t NEG3, const int j_even, const int gi, f2_t (&p)[7])
+{
+    f2_t dx, dy, dz;
+    if (MODE == kModeComp) {
+        dx = f2_add(f2_sub(X, I.x), f2_sub(LX, I.lx));
+        dy = f2_add(f2_sub(Y, I.y), f2_sub(LY, I.ly));
+        dz = f2_add(f2_sub(Z, I.z), f2_sub(LZ, I.lz));
+    } else {
+        dx = f2_sub(X, I.x);
+        dy = f2_sub(Y, I.y);
+        dz = f2_sub(Z, I.z);
+    }
+    const f2_t dvx = f2_sub(VX, I.vx), dvy = f2_sub(VY, I.vy), dvz = f2_sub(VZ, I.vz);
+    const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, E2)));
+    float r2a, r2b;
+    f2_unpack(r2, r2a, r2b);
+    float ra = rsqrt_mufu(r2a), rb = rsqrt_mufu(r2b);
+    if (SELF) {
+        ra = (j_even == gi) ? 0.0f : ra;
+        rb = (j_even + 1 == gi) ? 0.0f : rb;
+    }
+    const f2_t rinv = f2_pack(ra, rb);
+    const f2_t xv = f2_fma(dz, dvz, f2_fma(dy, dvy, f2_mul(dx, dvx)));
+    const f2_t rinv2 = f2_mul(rinv, rinv);
+    const f2_t mr = f2_mul(M, rinv);
+    const f2_t mr3 = f2_mul(mr, rinv2);
+    const f2_t wn = f2_mul(f2_mul(xv, rinv2), NEG3);  // -3 (dx.dv) r^-2
+    p[0] = f2_fma(mr3, dx, p[0]);
+    p[1] = f2_fma(mr3, dy, p[1]);
+    p[2] = f2_fma(mr3, dz, p[2]);
+    p[3] = f2_fma(mr3, f2_fma(wn, dx, dvx), p[3]);
+    p[4] = f2_fma(mr3, f2_fma(wn, dy, dvy), p[4]);
+    p[5] = f2_fma(mr3, f2_fma(wn, dz, dvz), p[5]);
+    p[6] = f2_sub(p[6], mr);
+}
+
+// Structure-of-arrays copy of one tile: x y z m vx vy vz (lx ly lz).
+template <int MODE>
+struct SoaTile {
+    static constexpr int NA = (MODE == kModeComp) ? 10 : 7;
+    float a[NA][kJTile];
+};
+
+template <int MODE, int IPT, int PF, bool SELF>
+__device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j0, const I2 (&I)[IPT],
+                                             const int (&gi)[IPT], const f2_t E2, const f2_t NEG3,
+                                             float (&tot)[IPT][7], float (&lo)[IPT][7])
+{
+#pragma unroll 1
+    for (int jb = 0; jb < kJTile; jb += PF) {
+        f2_t p[IPT][7];
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) p[u][c] = 0ull;
+#pragma unroll 2
+        for (int jj = 0; jj < PF; jj += 4) {
+            f2_t v[SoaTile<MODE>::NA][2];
+#pragma unroll
+            for (int a = 0; a < SoaTile<MODE>::NA; ++a) {
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&T.a[a][jb + jj]);
+                v[a][0] = q.x;
+                v[a][1] = q.y;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int u = 0; u < IPT; ++u)
+                    pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
+                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 3][h] : 0ull,
+                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 2][h] : 0ull,
+                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 1][h] : 0ull, I[u], E2,
+                                             NEG3, j0 + jb + jj + 2 * h, gi[u], p[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                float e, o;
+                f2_unpack(p[u][c], e, o);
+                const float part = e + o;
+                if (MODE == kModeComp)
+                    fold_ds(tot[u][c], lo[u][c], part);
+                else
+                    tot[u][c] += part;
+            }
+    }
+}
+
+template <int MODE, int NT, int IPT, int PF>
+__global__ void __launch_bounds__(NT) force_kernel_x2(const ForceParams P)
+{
+    constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
+    constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
+    static_assert(kJTile % PF == 0 && PF % 4 == 0, "fold length");
+    __shared__ __align__(128) float4 sj[2][NARR][kJTile];
+    __shared__ __align__(16) SoaTile<MODE> soa;
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int t_begin = blockIdx.y * P.tiles_per_split;
+    const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
+    const f2_t E2 = f2_pack(P.eps2, P.eps2);
+    const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
+
+    I2 I[IPT];
+    int gi[IPT];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        int idx = -1;
+        if (q < P.n_act) {
+            idx = P.active[q];
+            if (idx < 0 || idx >= P.n) {
+                atomicOr(&P.st->flags, kFlagBadIndex);
+                P.st->bad_index = q;
+                idx = -1;
+            }
+        }
+        gi[u] = idx;
+        const int l = idx >= 0 ? idx : 0;
+        const float4 xp = P.posm[l], vp = P.vel[l];
+        I[u].x = f2_pack(xp.x, xp.x);
+        I[u].y = f2_pack(xp.y, xp.y);
+        I[u].z = f2_pack(xp.z, xp.z);
+        I[u].vx = f2_pack(vp.x, vp.x);
+        I[u].vy = f2_pack(vp.y, vp.y);
+        I[u].vz = f2_pack(vp.z, vp.z);
+        if (MODE == kModeComp) {
+            const float4 lp = P.poslo[l];
+            I[u].lx = f2_pack(lp.x, lp.x);
+            I[u].ly = f2_pack(lp.y, lp.y);
+            I[u].lz = f2_pack(lp.z, lp.z);
+        }
+    }
+    float tot[IPT][7], lo[IPT][7];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            tot[u][c] = 0.0f;
+            lo[u][c] = 0.0f;
+        }
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int b) {
+        mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
+        const size_t off = static_cast<size_t>(tile) * kJTile;
+        bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
+        bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
+        if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+    };
+
+    bool ok = true;
+    int it_stop = 0;
+    if (tid == 0 && t_begin < t_end && !P.skip_first_copy) issue(t_begin, 0);
+    for (int t = t_begin; t < t_end; ++t) {
+        const int it = t - t_begin;
+        const int b = it & 1;
+        if (tid == 0 && t + 1 < t_end) issue(t + 1, b ^ 1);
+        ok = mbar_wait_bounded(&bar[b], (it >> 1) & 1);
+        if (ok) {
+            for (int e = tid; e < kJTile; e += NT) {
+                const float4 pv = sj[b][0][e], vv = sj[b][1][e];
+                soa.a[0][e] = pv.x;
+                soa.a[1][e] = pv.y;
+                soa.a[2][e] = pv.z;
+                soa.a[3][e] = pv.w;
+                soa.a[4][e] = vv.x;
+                soa.a[5][e] = vv.y;
+                soa.a[6][e] = vv.z;
+                if (MODE == kModeComp) {
+                    const float4 lv = sj[b][NARR - 1][e];
+                    soa.a[7][e] = lv.x;
+                    soa.a[8][e] = lv.y;
+                    soa.a[9][e] = lv.z;
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            it_stop = it;
+            break;
+        }
+        const int j0 = t * kJTile;
+        bool self_tile = false;
+#pragma unroll
+        for (int u = 0; u < IPT; ++u) self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
+        if (self_tile)
+            tile_sums_x2<MODE, IPT, PF, true>(soa, j0, I, gi, E2, NEG3, tot, lo);
+        else
+            tile_sums_x2<MODE, IPT, PF, false>(soa, j0, I, gi, E2, NEG3, tot, lo);
+        __syncthreads();
+    }
+
+    if (!ok) {
+        if (tid == 0) {
+            const int b = it_stop & 1;
+            mbar_wait_bounded(&bar[b], (it_stop >> 1) & 1);
+            if (t_begin + it_stop + 1 < t_end) mbar_wait_bounded(&bar[b ^ 1], ((it_stop + 1) >> 1) & 1);
+            atomicOr(&P.st->flags, kFlagTimeout);
+        }
+        return;
+    }
+
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        if (q >= P.n_act) continue;
+        if (gridDim.y == 1) {
+            double r[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                r[c] = (MODE == kModeComp) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
+                                           : static_cast<double>(tot[u][c]);
+            double *pa = P.acc + 3 * static_cast<size_t>(q);
+            double *pk = P.jerk + 3 * static_cast<size_t>(q);
+            pa[0] = r[0];
+            pa[1] = r[1];
+            pa[2] = r[2];
+            pk[0] = r[3];
+            pk[1] = r[4];
+            pk[2] = r[5];
+            P.pot[q] = r[6];
+        } else {
+            constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+            float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * P.n_act + q;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                base[static_cast<size_t>(c) * P.n_act] = tot[u][c];
+                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * P.n_act] = lo[u][c];
+            }
+        }
+    }
+}
+
+}  // namespace nb

@@ -113,6 +113,22 @@ cudaError_t pad_jstream_launch(const JStream &J, int64_t n, cudaStream_t s, int6
 // a[i] = i for 0 <= i < n.
 cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches);
 
+// ---- adjoint.cu: reverse mode of a shared-step rollout ----
+struct DiffGrads {
+    double *gx[3], *gv[3], *ga[3], *gk[3];  // gradients of the state (x, v, a, k), SoA
+    double *gxp[3], *gvp[3];                // gradients of the predicted x, v
+    double *gm;                             // gradient of the masses
+    float4 *gA, *gK;                        // upstream of the force (n_pad, zero padded)
+};
+cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, float eps2, cudaStream_t s,
+                             int64_t *launches);
+cudaError_t adj_correct_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches);
+cudaError_t adj_predict_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches);
+cudaError_t adj_init_launch(const DiffGrads &G, int64_t n, cudaStream_t s, int64_t *launches);
+cudaError_t loss_launch(const State &S, double eps2, const DiffGrads &G, double *lval, double *loss,
+                        cudaStream_t s, int64_t *launches);
+cudaError_t set_time_launch(const State &S, int64_t tick, int level, cudaStream_t s, int64_t *launches);
+
 // Row-major n x 3 <-> three component arrays.
 cudaError_t aos_to_soa_launch(const double *aos, double *c0, double *c1, double *c2, int64_t n,
                               cudaStream_t s, int64_t *launches);

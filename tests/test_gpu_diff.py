@@ -1,0 +1,65 @@
+"""The hand-written adjoint of the shared-step rollout against the FP64 reverse-mode
+oracle (itself pinned to finite differences of the C oracle, tests/test_oracle_adjoint.py)."""
+import numpy as np
+import pytest
+
+from oracle import adjoint
+from synthetic import plummer_sphere
+from tests.gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+EPS2 = (1.0 / 128) ** 2
+LEVEL, STEPS = 9, 256
+
+
+def _gpu_grad(m, x, v, steps=STEPS, ck=16, mode=0):
+    from paper_astro_ph_0702058_gb300 import nbody_diff_rollout
+    n = len(m)
+    loss = np.zeros(1)
+    gx, gv, gm = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    nbody_diff_rollout(n, m, x, v, EPS2, LEVEL, steps, ck, mode, loss, gx, gv, gm)
+    return loss[0], gx, gv, gm
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_matches_fp64_reverse_mode_n64(mode):
+    """N = 64, eps = 1/128, 256 steps of dt = 1/512: loss and dL/d(x0, v0, m)."""
+    need_gpu()
+    m, x, v = plummer_sphere(64, 12)
+    m = m * np.random.default_rng(3).uniform(0.8, 1.2, 64)
+    L, gx, gv, gm = _gpu_grad(m, x, v, mode=mode)
+    rL, rgx, rgv, rgm = adjoint.rollout_grad(m, x, v, EPS2, 2.0 ** -LEVEL, STEPS)
+    print(f"\nmode {mode}: loss rel err {abs(L - rL) / abs(rL):.2e}, grad rel err x {_rel(gx, rgx):.2e} "
+          f"v {_rel(gv, rgv):.2e} m {_rel(gm, rgm):.2e}")
+    assert abs(L - rL) <= 1e-6 * abs(rL)
+    for g, r in ((gx, rgx), (gv, rgv), (gm, rgm)):
+        assert _rel(g, r) < 1e-4
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    need_gpu()
+    m, x, v = plummer_sphere(96, 13)
+    outs = [_gpu_grad(m, x, v, steps=40, ck=ck) for ck in (1, 7, 16, 40)]
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_autograd_function():
+    torch = need_gpu()
+    from paper_astro_ph_0702058_gb300.autodiff import rollout_loss
+    m, x, v = plummer_sphere(128, 14)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    vt = torch.tensor(v, device="cuda", requires_grad=True)
+    mt = torch.tensor(m, device="cuda", requires_grad=True)
+    loss = rollout_loss(xt, vt, mt, steps=32)
+    (3.0 * loss).backward()
+    L, gx, gv, gm = _gpu_grad(m, x, v, steps=32)
+    assert abs(loss.item() - L) == 0.0
+    np.testing.assert_array_equal(xt.grad.cpu().numpy(), 3.0 * gx)
+    np.testing.assert_array_equal(vt.grad.cpu().numpy(), 3.0 * gv)
+    np.testing.assert_array_equal(mt.grad.cpu().numpy(), 3.0 * gm)
