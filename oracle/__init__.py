@@ -64,6 +64,9 @@ def lib():
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             L.orc_force.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I32, _D, _D, _D]
+            L.orc_force_fp32_terms.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I32, _D, _D, _D]
+            L.orc_rsqrt_rn_f32.argtypes = [C.c_float]
+            L.orc_rsqrt_rn_f32.restype = C.c_float
             L.orc_predict.argtypes = [C.c_int64, _D, _D, _D, _D, _I64, C.c_int64, C.c_int, _D, _D]
             L.orc_dt_initial.argtypes = [_D, _D, C.c_double]
             L.orc_dt_initial.restype = C.c_double
@@ -122,6 +125,28 @@ def force(m, x, v, eps2, active=None):
     lib().orc_force(n, _p(m, _D), _p(x, _D), _p(v, _D), float(eps2), na, _p(act, _I32),
                     _p(acc, _D), _p(jerk, _D), _p(pot, _D))
     return acc, jerk, pot
+
+
+def force_fp32_terms(m, x, v, eps2, active=None):
+    """(acc, jerk, pot) as the FP64 sums of the FP32 pair terms of the compensated pair term
+    formed with correctly rounded operations in a fixed order (the summation check)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    act = np.arange(n, dtype=np.int32) if active is None else np.ascontiguousarray(active, dtype=np.int32)
+    na = act.shape[0]
+    acc = np.zeros((na, 3))
+    jerk = np.zeros((na, 3))
+    pot = np.zeros(na)
+    lib().orc_force_fp32_terms(n, _p(m, _D), _p(x, _D), _p(v, _D), float(eps2), na, _p(act, _I32),
+                               _p(acc, _D), _p(jerk, _D), _p(pot, _D))
+    return acc, jerk, pot
+
+
+def rsqrt_rn_f32(r2):
+    """Correctly rounded single-precision 1/sqrt(r2)."""
+    return np.float32(lib().orc_rsqrt_rn_f32(float(np.float32(r2))))
 
 
 def predict(x, v, a, k, t_tick, t_new, lmax):

@@ -73,6 +73,112 @@ void orc_force(int64_t n, const double *m, const double *x, const double *v,
     }
 }
 
+/* Decomposes a positive finite float g as G * 2^e with G a 24-bit integer. */
+static void f32_parts(float g, uint64_t *G, int *e)
+{
+    int k;
+    const float fr = frexpf(g, &k); /* g = fr * 2^k, 0.5 <= fr < 1 */
+    *G = (uint64_t)ldexpf(fr, 24);
+    *e = k - 24;
+}
+
+/* Sign of mid^2 * r2 - 1, mid the midpoint of the positive floats a < b,
+ * computed exactly in 128-bit integers. */
+static int mid_sq_times_cmp1(float a, float b, float r2)
+{
+    uint64_t A, B, R;
+    int ea, eb, er;
+    f32_parts(a, &A, &ea);
+    f32_parts(b, &B, &eb);
+    f32_parts(r2, &R, &er);
+    const int e0 = ea < eb ? ea : eb;
+    /* a + b = S * 2^e0, mid = S * 2^(e0 - 1), S < 2^26 */
+    const uint64_t S = (A << (ea - e0)) + (B << (eb - e0));
+    const unsigned __int128 P = (unsigned __int128)(S * S) * R; /* < 2^76 */
+    const int K = 2 * (e0 - 1) + er;                            /* mid^2 r2 = P * 2^K */
+    if (K >= 0) return 1;                                        /* P >= 1 */
+    if (-K >= 127) return -1;
+    const unsigned __int128 one = (unsigned __int128)1 << (-K);
+    return P < one ? -1 : (P > one ? 1 : 0);
+}
+
+float orc_rsqrt_rn_f32(float r2)
+{
+    if (!(r2 > 0.0f) || !isfinite(r2) || !isnormal(r2)) return NAN;
+    float f = (float)(1.0 / sqrt((double)r2));
+    for (int it = 0; it < 8; it++) {
+        /* 1/sqrt(r2) > mid  <=>  mid^2 r2 < 1 (everything positive) */
+        const float up = nextafterf(f, INFINITY);
+        if (mid_sq_times_cmp1(f, up, r2) < 0) {
+            f = up;
+            continue;
+        }
+        const float dn = nextafterf(f, 0.0f);
+        if (mid_sq_times_cmp1(dn, f, r2) > 0) {
+            f = dn;
+            continue;
+        }
+        break; /* a tie (mid^2 r2 == 1) would need S = 1; S is odd and > 1 */
+    }
+    return f;
+}
+
+/* Neumaier's compensated summation step (Neumaier 1974). */
+static void neumaier_add(double *s, double *c, double t)
+{
+    const double u = *s + t;
+    if (fabs(*s) >= fabs(t))
+        *c += (*s - u) + t;
+    else
+        *c += (t - u) + *s;
+    *s = u;
+}
+
+void orc_force_fp32_terms(int64_t n, const double *m, const double *x, const double *v,
+                          double eps2, int64_t n_act, const int32_t *active,
+                          double *acc, double *jerk, double *pot)
+{
+    const float e2 = (float)eps2;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n_act; q++) {
+        const int64_t i = active[q];
+        float hi_i[3], lo_i[3], u_i[3];
+        for (int c = 0; c < 3; c++) {
+            hi_i[c] = (float)x[3 * i + c];
+            lo_i[c] = (float)(x[3 * i + c] - (double)hi_i[c]);
+            u_i[c] = (float)v[3 * i + c];
+        }
+        double s[7] = {0}, cmp[7] = {0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            float dx[3], dv[3];
+            for (int c = 0; c < 3; c++) {
+                const float hj = (float)x[3 * j + c];
+                const float lj = (float)(x[3 * j + c] - (double)hj);
+                dx[c] = (hj - hi_i[c]) + (lj - lo_i[c]);
+                dv[c] = (float)v[3 * j + c] - u_i[c];
+            }
+            const float r2 = fmaf(dx[2], dx[2], fmaf(dx[1], dx[1], fmaf(dx[0], dx[0], e2)));
+            const float rinv = orc_rsqrt_rn_f32(r2);
+            const float xv = fmaf(dx[2], dv[2], fmaf(dx[1], dv[1], dx[0] * dv[0]));
+            const float rinv2 = rinv * rinv;
+            const float mr = (float)m[j] * rinv;
+            const float mr3 = mr * rinv2;
+            const float w = 3.0f * (xv * rinv2);
+            for (int c = 0; c < 3; c++) {
+                neumaier_add(&s[c], &cmp[c], (double)(mr3 * dx[c]));
+                neumaier_add(&s[3 + c], &cmp[3 + c], (double)(mr3 * fmaf(-w, dx[c], dv[c])));
+            }
+            neumaier_add(&s[6], &cmp[6], (double)(-mr));
+        }
+        for (int c = 0; c < 3; c++) {
+            if (acc) acc[3 * q + c] = s[c] + cmp[c];
+            if (jerk) jerk[3 * q + c] = s[3 + c] + cmp[3 + c];
+        }
+        if (pot) pot[q] = s[6] + cmp[6];
+    }
+}
+
 /* Predictor, Sect. 2: x_p = x + v dt + a dt^2/2 + k dt^3/6,
  *                     v_p = v + a dt + k dt^2/2,  dt = t_new - t_i.      */
 void orc_predict(int64_t n, const double *x, const double *v, const double *a,

@@ -40,6 +40,27 @@ void orc_force(int64_t n, const double *m, const double *x, const double *v,
                double eps2, int64_t n_act, const int32_t *active,
                double *acc, double *jerk, double *pot);
 
+/* Correctly rounded (to nearest, ties to even) single-precision 1/sqrt(r2)
+ * for a positive normal float r2, by exact integer comparison of squared
+ * rounding midpoints against 1/r2.  Returns NaN for r2 <= 0 or non-finite. */
+float orc_rsqrt_rn_f32(float r2);
+
+/* The summation check of the compensated force (reading of the 1e-10
+ * summation bound): the same listed sums as orc_force, but every pair term is
+ * first formed in single precision exactly as the compensated pair term
+ * computes it with correctly rounded operations in a fixed order:
+ *   hi = fl32(x), lo = fl32(x - hi), u = fl32(v), mu = fl32(m), e2 = fl32(eps2);
+ *   dx = (hi_j - hi_i) + (lo_j - lo_i);  dv = u_j - u_i;
+ *   r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, e2)));  rinv = rsqrt_rn(r2);
+ *   xv = fma(dz, dvz, fma(dy, dvy, dx * dvx));
+ *   mr = mu_j * rinv;  mr3 = mr * (rinv * rinv);  w = 3 * (xv * (rinv * rinv));
+ *   terms: mr3 * dx_c,  mr3 * fma(-w, dx_c, dv_c),  -mr.
+ * Each term is then summed over j in ascending order in FP64 with Neumaier's
+ * compensation, so the result is the sum of those FP32 terms to ~1e-16. */
+void orc_force_fp32_terms(int64_t n, const double *m, const double *x, const double *v,
+                          double eps2, int64_t n_act, const int32_t *active,
+                          double *acc, double *jerk, double *pot);
+
 /* Predictor of Sect. 2: every particle from its own time t_tick[i] to t_new. */
 void orc_predict(int64_t n, const double *x, const double *v, const double *a,
                  const double *k, const int64_t *t_tick, int64_t t_new, int lmax,
