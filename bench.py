@@ -389,6 +389,45 @@ def force_only(args):
     print(json.dumps({"force_only": args.n, "modes": args.modes}))
 
 
+def c2_sweep(args):
+    """C2 force-only sweep: N = 65536 Plummer sphere (seed 2, eps = 1/256), one nbody_force per
+    call on a seeded sorted uniform sample of n_act particles, n_act in {1, 32, 1024, 1594
+    (about the mean block 0.2 N^0.81), 32768, 65536}; interactions/s = n_act (N - 1) / t, t the
+    median CUDA-event time of 20 calls after 3 warm-up calls on the context stream, plain and
+    compensated.  The 3 MB j-stream stays resident in L2 across calls: that is the regime of the
+    block steps this sweep stands for, so no flush between calls."""
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import active_subset, plummer_sphere
+    n, eps2 = 65536, (1.0 / 256) ** 2
+    m, x, v = plummer_sphere(n, 2)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for mode in args.modes.split(","):
+        with torch.cuda.stream(stream), Simulation(m, x, v, eps2, eta=0.02, mode=mode, stream=stream) as sim:
+            sim.predict(0.0)
+            for n_act in (1, 32, 1024, 1594, 32768, 65536):
+                act = torch.from_numpy(active_subset(n, n_act, 2)).to("cuda")
+                for _ in range(3):
+                    sim.force(act, n_act)
+                ts = []
+                for _ in range(20):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sim.force(act, n_act)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1) * 1e-3)
+                t = statistics.median(ts)
+                st = sim.stats()
+                rows.append({"mode": mode, "n_act": n_act, "us": t * 1e6, "interactions_per_s": n_act * (n - 1) / t,
+                             "threads": st["last_threads"], "i_block": st["last_i_per_thread"],
+                             "j_split": st["last_j_split"]})
+    print(json.dumps({"workload": "c2 force-only sweep", "n": n, "eps": 1.0 / 256, "rows": rows}), flush=True)
+
+
 def ensemble_workload(args):
     """C4: 512 independent Plummer clusters (sizes log-uniform in [256, 8192) from seed 4),
     eps = 1/256, eta = 0.02, integrated to t = 1/4 as one batched, graph-replayed run
@@ -452,8 +491,9 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
-    ap.add_argument("--workload", choices=["c3", "ensemble"], default="c3",
-                    help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run")
+    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep"], default="c3",
+                    help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run; "
+                         "c2-sweep: force-only rates against the block size at N = 65536")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--ens-sample", type=int, default=32, help="clusters run one context each, for comparison")
     ap.add_argument("--ens-mode", default="comp")
@@ -463,6 +503,9 @@ def main(argv=None):
         return
     if args.workload == "ensemble":
         ensemble_workload(args)
+        return
+    if args.workload == "c2-sweep":
+        c2_sweep(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

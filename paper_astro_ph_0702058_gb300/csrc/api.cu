@@ -219,7 +219,7 @@ int predict_internal(nbody_ctx *c, int64_t tick)
     if (tick < c->t_max)
         return fail(NBODY_EINVAL, "prediction time %lld ticks is before a particle time %lld",
                     static_cast<long long>(tick), static_cast<long long>(c->t_max));
-    NB_CUDA(predict_launch(c->S, c->J, tick, c->p.lmax, c->p.mode == kModeComp, c->s, &c->stats.kernel_launches),
+    NB_CUDA(predict_launch(c->S, c->J, tick, c->p.lmax, is_ds(c->p.mode), c->s, &c->stats.kernel_launches),
             "predictor launch");
     c->t_pred = tick;
     c->pred_valid = true;
@@ -261,7 +261,8 @@ int check_params(const nbody_params *p)
     if (!(p->eta > 0.0) || !std::isfinite(p->eta)) return fail(NBODY_EINVAL, "eta must be positive");
     if (p->lmin < 0 || p->lmax > 40 || p->lmin > p->lmax)
         return fail(NBODY_EINVAL, "need 0 <= lmin <= lmax <= 40 (got %d, %d)", p->lmin, p->lmax);
-    if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP) return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
+    if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP && p->mode != NBODY_MODE_SUMCHECK)
+        return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
     if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256)
         return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128 or 256");
     if (p->i_block != 0 && p->i_block != 1 && p->i_block != 2 && p->i_block != 4)

@@ -14,6 +14,10 @@ cudaError_t reduce_plain(const float *part, int split, int n_act, double *acc, d
                          cudaStream_t s);
 cudaError_t reduce_comp(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
                         cudaStream_t s);
+cudaError_t force_dispatch_check(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s);
+int force_occupancy_check(int threads, int ipt);
+cudaError_t reduce_check(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
+                         cudaStream_t s);
 
 int g_skip_first_copy = 0;  // test hook (nbody_debug_skip_tile_copy)
 
@@ -30,12 +34,14 @@ int shape_index(int threads, int ipt)
 // every device this library runs on is the same sm_103 part).
 int occupancy(int mode, int threads, int ipt)
 {
-    static int cache[2][9];
-    static bool filled[2][9];
+    static int cache[3][9];
+    static bool filled[3][9];
     const int si = shape_index(threads, ipt);
-    if (si < 0) return 0;
+    if (si < 0 || mode < 0 || mode > 2) return 0;
     if (!filled[mode][si]) {
-        cache[mode][si] = mode == kModeComp ? force_occupancy_comp(threads, ipt) : force_occupancy_plain(threads, ipt);
+        cache[mode][si] = mode == kModeComp    ? force_occupancy_comp(threads, ipt)
+                          : mode == kModeCheck ? force_occupancy_check(threads, ipt)
+                                               : force_occupancy_plain(threads, ipt);
         filled[mode][si] = true;
     }
     return cache[mode][si];
@@ -94,7 +100,7 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
 size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
 {
     if (cfg.split <= 1) return 0;
-    const size_t nc = mode == kModeComp ? 14 : 7;
+    const size_t nc = is_ds(mode) ? 14 : 7;
     return static_cast<size_t>(cfg.split) * nc * static_cast<size_t>(n_act) * sizeof(float);
 }
 
@@ -120,12 +126,15 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     P.part = static_cast<float *>(partials);
     P.st = st;
     P.skip_first_copy = g_skip_first_copy;
-    cudaError_t e = mode == kModeComp ? force_dispatch_comp(P, c, s) : force_dispatch_plain(P, c, s);
+    cudaError_t e = mode == kModeComp    ? force_dispatch_comp(P, c, s)
+                    : mode == kModeCheck ? force_dispatch_check(P, c, s)
+                                         : force_dispatch_plain(P, c, s);
     if (e != cudaSuccess) return e;
     ++*launches;
     if (c.split > 1) {
-        e = mode == kModeComp ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s)
-                              : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s);
+        e = mode == kModeComp    ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s)
+            : mode == kModeCheck ? reduce_check(P.part, c.split, P.n_act, acc, jerk, pot, s)
+                                 : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s);
         if (e != cudaSuccess) return e;
         ++*launches;
     }

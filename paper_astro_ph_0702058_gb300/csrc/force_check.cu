@@ -1,0 +1,19 @@
+// Instantiates the force kernels of the summation-check mode (see force_impl.cuh).
+#include "force_dispatch.cuh"
+
+namespace nb {
+
+cudaError_t force_dispatch_check(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+    return force_dispatch<kModeCheck>(P, cfg, s);
+}
+
+int force_occupancy_check(int threads, int ipt) { return force_occupancy<kModeCheck>(threads, ipt); }
+
+cudaError_t reduce_check(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
+                         cudaStream_t s)
+{
+    return reduce_launch<kModeCheck>(part, split, n_act, acc, jerk, pot, s);
+}
+
+}  // namespace nb

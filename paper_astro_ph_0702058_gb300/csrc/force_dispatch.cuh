@@ -16,7 +16,7 @@ template <int MODE, int NT, int IPT>
 cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
 {
     dim3 grid(cfg.n_iblk, cfg.split);
-    if (NB_PACKED)
+    if constexpr (NB_PACKED && MODE != kModeCheck)
         force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
     else
         force_kernel<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
@@ -26,10 +26,11 @@ cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, 
 template <int MODE, int NT, int IPT>
 int occupancy_instance(int *blocks)
 {
-    if (NB_PACKED)
+    if constexpr (NB_PACKED && MODE != kModeCheck)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             blocks, force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value>, NT, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
+    else
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
                                                          NT, 0);
 }
 

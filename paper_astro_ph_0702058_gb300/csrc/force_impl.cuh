@@ -68,7 +68,7 @@ __device__ __forceinline__ void pair_term(const float4 pj, const float4 vj, cons
                                           const float eps2, const int j, const int i, float (&p)[7])
 {
     float dx, dy, dz;
-    if (MODE == kModeComp) {
+    if (is_ds(MODE)) {
         dx = (pj.x - xi.x) + (lj.x - li.x);
         dy = (pj.y - xi.y) + (lj.y - li.y);
         dz = (pj.z - xi.z) + (lj.z - li.z);
@@ -108,10 +108,64 @@ __device__ __forceinline__ void fold_ds(float &hi, float &lo, const float x)
     lo = lo + e;
 }
 
+// The same fold with round-to-nearest intrinsics, which the compiler never
+// fuses with the operations around them.
+__device__ __forceinline__ void fold_ds_rn(float &hi, float &lo, const float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// Summation-check pair term: the compensated pair term with every operation
+// written as a round-to-nearest intrinsic in a fixed order and the correctly
+// rounded reciprocal square root, each of the 7 terms folded into (tot, lo)
+// on its own.  A CPU that follows the same order forms the same FP32 terms,
+// so the only difference left is the summation.
+//   dx = (xj_hi - xi_hi) + (xj_lo - xi_lo);  dv = vj - vi
+//   r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));  rinv = rsqrt_rn(r2)
+//   xv = fma(dz, dvz, fma(dy, dvy, dx * dvx))
+//   mr = m * rinv;  mr3 = mr * (rinv * rinv);  w = 3 * (xv * (rinv * rinv))
+//   terms: mr3 * dx_c,  mr3 * fma(-w, dx_c, dv_c),  -mr
+template <bool SELF>
+__device__ __forceinline__ void pair_term_check(const float4 pj, const float4 vj, const float4 lj,
+                                                const float4 xi, const float4 vi, const float4 li,
+                                                const float eps2, const int j, const int i, float (&tot)[7],
+                                                float (&lo)[7])
+{
+    const float dx = __fadd_rn(__fsub_rn(pj.x, xi.x), __fsub_rn(lj.x, li.x));
+    const float dy = __fadd_rn(__fsub_rn(pj.y, xi.y), __fsub_rn(lj.y, li.y));
+    const float dz = __fadd_rn(__fsub_rn(pj.z, xi.z), __fsub_rn(lj.z, li.z));
+    const float dvx = __fsub_rn(vj.x, vi.x);
+    const float dvy = __fsub_rn(vj.y, vi.y);
+    const float dvz = __fsub_rn(vj.z, vi.z);
+    if (SELF && j == i) return;  // j = i contributes nothing
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, eps2)));
+    const float rinv = __frsqrt_rn(r2);
+    const float xv = __fmaf_rn(dz, dvz, __fmaf_rn(dy, dvy, __fmul_rn(dx, dvx)));
+    const float rinv2 = __fmul_rn(rinv, rinv);
+    const float mr = __fmul_rn(pj.w, rinv);
+    const float mr3 = __fmul_rn(mr, rinv2);
+    const float w = __fmul_rn(3.0f, __fmul_rn(xv, rinv2));
+    fold_ds_rn(tot[0], lo[0], __fmul_rn(mr3, dx));
+    fold_ds_rn(tot[1], lo[1], __fmul_rn(mr3, dy));
+    fold_ds_rn(tot[2], lo[2], __fmul_rn(mr3, dz));
+    fold_ds_rn(tot[3], lo[3], __fmul_rn(mr3, __fmaf_rn(-w, dx, dvx)));
+    fold_ds_rn(tot[4], lo[4], __fmul_rn(mr3, __fmaf_rn(-w, dy, dvy)));
+    fold_ds_rn(tot[5], lo[5], __fmul_rn(mr3, __fmaf_rn(-w, dz, dvz)));
+    fold_ds_rn(tot[6], lo[6], -mr);
+}
+
 // Fold length (pairs per FP32 partial) of each mode.
 template <int MODE>
 struct FoldLen {
     static constexpr int value = NB_FOLD;
+};
+template <>
+struct FoldLen<kModeCheck> {
+    static constexpr int value = 1;
 };
 
 // Sums over one staged tile of kJTile j (starting at global index j0).
@@ -121,6 +175,16 @@ __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, co
                                           const float4 (&li)[IPT], const int (&gi)[IPT], const float eps2,
                                           float (&tot)[IPT][7], float (&lo)[IPT][7])
 {
+    if constexpr (MODE == kModeCheck) {
+#pragma unroll 4
+        for (int jj = 0; jj < kJTile; ++jj) {
+            const float4 pj = sp[jj], vj = sv[jj], lj = sl[jj];
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+                pair_term_check<SELF>(pj, vj, lj, xi[u], vi[u], li[u], eps2, j0 + jj, gi[u], tot[u], lo[u]);
+        }
+        return;
+    }
 #pragma unroll 1
     for (int jb = 0; jb < kJTile; jb += PF) {
         float p[IPT][7];
@@ -132,7 +196,7 @@ __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, co
         for (int jj = 0; jj < PF; ++jj) {
             const float4 pj = sp[jb + jj];
             const float4 vj = sv[jb + jj];
-            const float4 lj = (MODE == kModeComp) ? sl[jb + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 lj = (is_ds(MODE)) ? sl[jb + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < IPT; ++u)
                 pair_term<MODE, SELF>(pj, vj, lj, xi[u], vi[u], li[u], eps2, j0 + jb + jj, gi[u], p[u]);
@@ -141,7 +205,7 @@ __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, co
         for (int u = 0; u < IPT; ++u)
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
-                if (MODE == kModeComp)
+                if (is_ds(MODE))
                     fold_ds(tot[u][c], lo[u][c], p[u][c]);
                 else
                     tot[u][c] += p[u][c];
@@ -152,7 +216,7 @@ __device__ __forceinline__ void tile_sums(const float4 *sp, const float4 *sv, co
 template <int MODE, int NT, int IPT, int PF>
 __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
 {
-    constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
+    constexpr int NARR = (is_ds(MODE)) ? 3 : 2;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
     static_assert(kJTile % PF == 0, "fold length must divide the tile");
     __shared__ __align__(128) float4 sj[2][NARR][kJTile];
@@ -180,7 +244,7 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
         const int l = idx >= 0 ? idx : 0;
         xi[u] = P.posm[l];
         vi[u] = P.vel[l];
-        li[u] = (MODE == kModeComp) ? P.poslo[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        li[u] = (is_ds(MODE)) ? P.poslo[l] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
     float tot[IPT][7], lo[IPT][7];
@@ -204,7 +268,7 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
         const size_t off = static_cast<size_t>(tile) * kJTile;
         bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
         bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
-        if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+        if (is_ds(MODE)) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
     };
 
     bool ok = true;
@@ -253,7 +317,7 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
             double r[7];
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                r[c] = (MODE == kModeComp) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
+                r[c] = (is_ds(MODE)) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
                                            : static_cast<double>(tot[u][c]);
             double *pa = P.acc + 3 * static_cast<size_t>(q);
             double *pk = P.jerk + 3 * static_cast<size_t>(q);
@@ -265,12 +329,12 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
             pk[2] = r[5];
             P.pot[q] = r[6];
         } else {
-            constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+            constexpr int NC = (is_ds(MODE)) ? 14 : 7;
             float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * P.n_act + q;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 base[static_cast<size_t>(c) * P.n_act] = tot[u][c];
-                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * P.n_act] = lo[u][c];
+                if (is_ds(MODE)) base[static_cast<size_t>(7 + c) * P.n_act] = lo[u][c];
             }
         }
     }
@@ -282,7 +346,7 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
                                        double *__restrict__ acc, double *__restrict__ jerk,
                                        double *__restrict__ pot)
 {
-    constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+    constexpr int NC = (is_ds(MODE)) ? 14 : 7;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n_act) return;
     double r[7];
@@ -292,7 +356,7 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
         for (int sp = 0; sp < split; ++sp) {
             const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
             s += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
-            if (MODE == kModeComp) s += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
+            if (is_ds(MODE)) s += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
         }
         r[c] = s;
     }
@@ -313,7 +377,7 @@ __global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int 
                                             double *__restrict__ acc, double *__restrict__ jerk,
                                             double *__restrict__ pot)
 {
-    constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+    constexpr int NC = (is_ds(MODE)) ? 14 : 7;
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= n_act) return;
@@ -325,7 +389,7 @@ __global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int 
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             r[c] += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
-            if (MODE == kModeComp) r[c] += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
+            if (is_ds(MODE)) r[c] += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
         }
     }
 #pragma unroll

@@ -20,6 +20,9 @@ constexpr int kJTile = 256;
 constexpr float kPadPosition = 1e15f;  // coordinate of the massless padding particles
 constexpr int kModePlain = NBODY_MODE_PLAIN;
 constexpr int kModeComp = NBODY_MODE_COMP;
+constexpr int kModeCheck = NBODY_MODE_SUMCHECK;
+// Modes that read the hi/lo position split and keep double-single sums.
+__host__ __device__ constexpr bool is_ds(int mode) { return mode != kModePlain; }
 
 // Device-side status word of a context (written by kernels, read by the host).
 enum : unsigned {
