@@ -182,7 +182,8 @@ def run_steps(sim, n, steps, warmup, stream, flush, host=None):
 
 
 KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_astro_ph_0702058_gb300/csrc/ptx.cuh",
-                  "paper_astro_ph_0702058_gb300/csrc/force.cu")
+                  "paper_astro_ph_0702058_gb300/csrc/force.cu", "paper_astro_ph_0702058_gb300/csrc/force_x2.cuh",
+                  "paper_astro_ph_0702058_gb300/csrc/force_dispatch.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic_n1048576.json")
 
 

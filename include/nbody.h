@@ -65,13 +65,19 @@ enum {
     NBODY_MODE_PLAIN = 0,  /* FP32 pair math on FP32 positions, FP32 accumulation           */
     NBODY_MODE_COMP = 1,   /* FP32 pair math on x_j - x_i formed from hi/lo splits of the
                               FP64 positions; double-single (compensated) accumulation      */
-    NBODY_MODE_SUMCHECK = 2 /* test mode for the compensated summation: the pair term of
+    NBODY_MODE_SUMCHECK = 2, /* test mode for the compensated summation: the pair term of
                               NBODY_MODE_COMP with the correctly rounded reciprocal square
                               root and no contracted operations, so that every FP32 term is
                               reproducible on a CPU, and every term folded into the
                               double-single sums on its own (the production mode sums 64
                               terms in FP32 first).  Slower; nbody_force / nbody_step only
                               (not the ensemble or the no-alloc entry point).              */
+    NBODY_MODE_SORTED = 3  /* ablation of the accumulation order (Sect. 6 of the paper): the
+                              plain-mode FP32 pair terms, formed with correctly rounded
+                              operations in a fixed order, sorted by magnitude per row and
+                              component and added in FP32 from the smallest.  One block per
+                              active particle; n <= 32768 (NBODY_EINVAL above).  nbody_force /
+                              nbody_step only.                                              */
 };
 
 typedef struct nbody_ctx nbody_ctx; /* opaque; owns all of its device memory */
@@ -81,7 +87,7 @@ typedef struct {
     double eta_init;  /* nu of Eq. (initTimestep); <= 0 means "same as eta"               */
     int lmin;         /* dt_max = 2^-lmin (paper: 0.125, lmin = 3)                          */
     int lmax;         /* dt_min = 2^-lmax (paper: 2^-26, lmax = 26); 0 <= lmin <= lmax <= 40 */
-    int mode;         /* NBODY_MODE_PLAIN, NBODY_MODE_COMP or NBODY_MODE_SUMCHECK            */
+    int mode;         /* NBODY_MODE_PLAIN, _COMP, _SUMCHECK or _SORTED                       */
     int strict;       /* nonzero: a step clamped at dt_min makes nbody_correct fail with
                          NBODY_EDTMIN (the step is still taken); zero: it is only counted */
     int i_block;      /* force tuning, 0 = automatic: i-particles per thread (1, 2 or 4)    */

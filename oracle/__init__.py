@@ -65,6 +65,7 @@ def lib():
             L.orc_get_threads.restype = C.c_int
             L.orc_force.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I32, _D, _D, _D]
             L.orc_force_fp32_terms.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I32, _D, _D, _D]
+            L.orc_force_sorted_fp32.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I32, _D, _D, _D]
             L.orc_rsqrt_rn_f32.argtypes = [C.c_float]
             L.orc_rsqrt_rn_f32.restype = C.c_float
             L.orc_predict.argtypes = [C.c_int64, _D, _D, _D, _D, _I64, C.c_int64, C.c_int, _D, _D]
@@ -141,6 +142,23 @@ def force_fp32_terms(m, x, v, eps2, active=None):
     pot = np.zeros(na)
     lib().orc_force_fp32_terms(n, _p(m, _D), _p(x, _D), _p(v, _D), float(eps2), na, _p(act, _I32),
                                _p(acc, _D), _p(jerk, _D), _p(pot, _D))
+    return acc, jerk, pot
+
+
+def force_sorted_fp32(m, x, v, eps2, active=None):
+    """(acc, jerk, pot) of the sorted-summation ablation: plain FP32 pair terms (correctly
+    rounded, fixed order) added in FP32 by increasing magnitude (Sect. 6 of the paper)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    act = np.arange(n, dtype=np.int32) if active is None else np.ascontiguousarray(active, dtype=np.int32)
+    na = act.shape[0]
+    acc = np.zeros((na, 3))
+    jerk = np.zeros((na, 3))
+    pot = np.zeros(na)
+    lib().orc_force_sorted_fp32(n, _p(m, _D), _p(x, _D), _p(v, _D), float(eps2), na, _p(act, _I32),
+                                _p(acc, _D), _p(jerk, _D), _p(pot, _D))
     return acc, jerk, pot
 
 

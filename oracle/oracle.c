@@ -179,6 +179,78 @@ void orc_force_fp32_terms(int64_t n, const double *m, const double *x, const dou
     }
 }
 
+static uint32_t f32_bits(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+/* Order by magnitude, then by the raw bits. */
+static int cmp_size(const void *pa, const void *pb)
+{
+    const uint32_t a = f32_bits(*(const float *)pa), b = f32_bits(*(const float *)pb);
+    const uint32_t ma = a & 0x7fffffffu, mb = b & 0x7fffffffu;
+    if (ma != mb) return ma < mb ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+void orc_force_sorted_fp32(int64_t n, const double *m, const double *x, const double *v,
+                           double eps2, int64_t n_act, const int32_t *active,
+                           double *acc, double *jerk, double *pot)
+{
+    const float e2 = (float)eps2;
+#pragma omp parallel
+    {
+        float *t[7];
+        for (int c = 0; c < 7; c++) t[c] = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < n_act; q++) {
+            const int64_t i = active[q];
+            float hi_i[3], u_i[3];
+            for (int c = 0; c < 3; c++) {
+                hi_i[c] = (float)x[3 * i + c];
+                u_i[c] = (float)v[3 * i + c];
+            }
+            int64_t cnt = 0;
+            for (int64_t j = 0; j < n; j++) {
+                if (j == i) continue;
+                float dx[3], dv[3];
+                for (int c = 0; c < 3; c++) {
+                    dx[c] = (float)x[3 * j + c] - hi_i[c];
+                    dv[c] = (float)v[3 * j + c] - u_i[c];
+                }
+                const float r2 = fmaf(dx[2], dx[2], fmaf(dx[1], dx[1], fmaf(dx[0], dx[0], e2)));
+                const float rinv = orc_rsqrt_rn_f32(r2);
+                const float xv = fmaf(dx[2], dv[2], fmaf(dx[1], dv[1], dx[0] * dv[0]));
+                const float rinv2 = rinv * rinv;
+                const float mr = (float)m[j] * rinv;
+                const float mr3 = mr * rinv2;
+                const float w = 3.0f * (xv * rinv2);
+                for (int c = 0; c < 3; c++) {
+                    t[c][cnt] = mr3 * dx[c];
+                    t[3 + c][cnt] = mr3 * fmaf(-w, dx[c], dv[c]);
+                }
+                t[6][cnt] = -mr;
+                cnt++;
+            }
+            float sum[7];
+            for (int c = 0; c < 7; c++) {
+                qsort(t[c], (size_t)cnt, sizeof(float), cmp_size);
+                float s = 0.0f;
+                for (int64_t k = 0; k < cnt; k++) s = s + t[c][k];
+                sum[c] = s;
+            }
+            for (int c = 0; c < 3; c++) {
+                if (acc) acc[3 * q + c] = (double)sum[c];
+                if (jerk) jerk[3 * q + c] = (double)sum[3 + c];
+            }
+            if (pot) pot[q] = (double)sum[6];
+        }
+        for (int c = 0; c < 7; c++) free(t[c]);
+    }
+}
+
 /* Predictor, Sect. 2: x_p = x + v dt + a dt^2/2 + k dt^3/6,
  *                     v_p = v + a dt + k dt^2/2,  dt = t_new - t_i.      */
 void orc_predict(int64_t n, const double *x, const double *v, const double *a,

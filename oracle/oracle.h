@@ -61,6 +61,18 @@ void orc_force_fp32_terms(int64_t n, const double *m, const double *x, const dou
                           double eps2, int64_t n_act, const int32_t *active,
                           double *acc, double *jerk, double *pot);
 
+/* Sorted-summation ablation (Sect. 6 of the paper: add the forces by size,
+ * smallest first).  The plain pair terms in single precision, from
+ * hi = fl32(x), u = fl32(v), mu = fl32(m), e2 = fl32(eps2):
+ *   dx = hi_j - hi_i;  dv = u_j - u_i;  then as orc_force_fp32_terms;
+ * for each listed i and each of the 7 components, the terms over j != i are
+ * sorted by magnitude (ties: by the raw bits as unsigned integers, so -x after
+ * x) and added in FP32 from the smallest.  Exact in the sense that every step
+ * is one correctly rounded single-precision operation. */
+void orc_force_sorted_fp32(int64_t n, const double *m, const double *x, const double *v,
+                           double eps2, int64_t n_act, const int32_t *active,
+                           double *acc, double *jerk, double *pot);
+
 /* Predictor of Sect. 2: every particle from its own time t_tick[i] to t_new. */
 void orc_predict(int64_t n, const double *x, const double *v, const double *a,
                  const double *k, const int64_t *t_tick, int64_t t_new, int lmax,

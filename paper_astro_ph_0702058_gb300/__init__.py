@@ -9,7 +9,8 @@ by callers, for device memory and streams.
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBODY_MODE_SUMCHECK, NBodyError,  # noqa: F401
+from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBODY_MODE_SORTED, NBODY_MODE_SUMCHECK,
+                   NBodyError,  # noqa: F401
                    nbody_diff_rollout,
                    nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
                    nbody_ens_init, nbody_ens_run, nbody_ens_set_shape, nbody_ens_step, nbody_ens_tune,
@@ -18,7 +19,8 @@ from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBODY_MODE_SUMCHECK, NBody
                    nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
                    nbody_strerror, nbody_sync)
 
-MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP, "sumcheck": NBODY_MODE_SUMCHECK}
+MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP, "sumcheck": NBODY_MODE_SUMCHECK,
+         "sorted": NBODY_MODE_SORTED}
 
 
 class Simulation:

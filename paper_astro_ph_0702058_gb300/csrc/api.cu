@@ -261,7 +261,8 @@ int check_params(const nbody_params *p)
     if (!(p->eta > 0.0) || !std::isfinite(p->eta)) return fail(NBODY_EINVAL, "eta must be positive");
     if (p->lmin < 0 || p->lmax > 40 || p->lmin > p->lmax)
         return fail(NBODY_EINVAL, "need 0 <= lmin <= lmax <= 40 (got %d, %d)", p->lmin, p->lmax);
-    if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP && p->mode != NBODY_MODE_SUMCHECK)
+    if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP && p->mode != NBODY_MODE_SUMCHECK &&
+        p->mode != NBODY_MODE_SORTED)
         return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
     if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256)
         return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128 or 256");
@@ -293,6 +294,8 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     if (!out || !m || !x || !v) return fail(NBODY_EINVAL, "nbody_init: null pointer argument");
     *out = nullptr;
     if (n < 1 || n > 2147483647LL) return fail(NBODY_EINVAL, "nbody_init: n = %lld out of range", static_cast<long long>(n));
+    if (p && p->mode == NBODY_MODE_SORTED && n > kSortedMaxN)
+        return fail(NBODY_EINVAL, "nbody_init: the sorted mode takes n <= %lld", static_cast<long long>(kSortedMaxN));
     if (!(eps2 >= 0.0) || !std::isfinite(eps2)) return fail(NBODY_EINVAL, "nbody_init: eps2 must be finite and >= 0");
     nbody_params prm;
     if (p) prm = *p;

@@ -25,9 +25,10 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
-#include "force_impl.cuh"
+#include "force_x2.cuh"
 #include "step_impl.cuh"
 
 namespace nb {
@@ -207,10 +208,14 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
     constexpr int NC = (MODE == kModeComp) ? 14 : 7;
     constexpr int PF = FoldLen<MODE>::value;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
+    constexpr bool kPacked = NB_PACKED != 0;
     __shared__ __align__(128) float4 sj[2][NARR][kJTile];
+    __shared__ __align__(16) typename std::conditional<kPacked, SoaTile<MODE>, char>::type soa;
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long s_w;
     const int tid = threadIdx.x;
+    const f2_t E2 = f2_pack(eps2, eps2);
+    const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -269,6 +274,21 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
             vi[u] = E.J.vel[l];
             li[u] = (MODE == kModeComp) ? E.J.poslo[l] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        I2 I[IPT];
+        if constexpr (kPacked) {
+#pragma unroll
+            for (int u = 0; u < IPT; ++u) {
+                I[u].x = f2_pack(xi[u].x, xi[u].x);
+                I[u].y = f2_pack(xi[u].y, xi[u].y);
+                I[u].z = f2_pack(xi[u].z, xi[u].z);
+                I[u].vx = f2_pack(vi[u].x, vi[u].x);
+                I[u].vy = f2_pack(vi[u].y, vi[u].y);
+                I[u].vz = f2_pack(vi[u].z, vi[u].z);
+                I[u].lx = f2_pack(li[u].x, li[u].x);
+                I[u].ly = f2_pack(li[u].y, li[u].y);
+                I[u].lz = f2_pack(li[u].z, li[u].z);
+            }
+        }
         float tot[IPT][7], lo_[IPT][7];
 #pragma unroll
         for (int u = 0; u < IPT; ++u)
@@ -284,6 +304,46 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
             const int b = g & 1;
             if (tid == 0 && t + 1 < t_end) issue(jt0 + t + 1, b ^ 1);
             ok = mbar_wait_bounded(&bar[b], (g >> 1) & 1);
+            if constexpr (kPacked) {
+                // same order as the single-system packed kernel: transpose, then the packed loop
+                if (ok) {
+                    for (int e = tid; e < kJTile; e += NT) {
+                        const float4 pv = sj[b][0][e], vv = sj[b][1][e];
+                        soa.a[0][e] = pv.x;
+                        soa.a[1][e] = pv.y;
+                        soa.a[2][e] = pv.z;
+                        soa.a[3][e] = pv.w;
+                        soa.a[4][e] = vv.x;
+                        soa.a[5][e] = vv.y;
+                        soa.a[6][e] = vv.z;
+                        if (MODE == kModeComp) {
+                            const float4 lv = sj[b][NARR - 1][e];
+                            soa.a[7][e] = lv.x;
+                            soa.a[8][e] = lv.y;
+                            soa.a[9][e] = lv.z;
+                        }
+                    }
+                }
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) {
+                        mbar_wait_bounded(&bar[b], (g >> 1) & 1);
+                        if (t + 1 < t_end) mbar_wait_bounded(&bar[b ^ 1], ((g + 1) >> 1) & 1);
+                        atomicOr(&E.st->flags, kFlagTimeout);
+                    }
+                    return;
+                }
+                const int j0 = static_cast<int>(jo) + t * kJTile;
+                bool self_tile = false;
+#pragma unroll
+                for (int u = 0; u < IPT; ++u)
+                    self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
+                if (self_tile)
+                    tile_sums_x2<MODE, IPT, PF, true>(soa, j0, I, gi, E2, NEG3, tot, lo_);
+                else
+                    tile_sums_x2<MODE, IPT, PF, false>(soa, j0, I, gi, E2, NEG3, tot, lo_);
+                __syncthreads();
+                continue;
+            }
             if (ok) {
                 const int j0 = static_cast<int>(jo) + t * kJTile;
                 bool self_tile = false;

@@ -55,13 +55,14 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     const int n_tiles = static_cast<int>(n_pad / kJTile);
     int threads = req_threads;
     int ipt = req_ipt;
-    // Large blocks: 4 i per thread amortise the shared-memory loads over more
-    // pairs (measured 6 % faster than 2 at N = 2^20); small blocks need more
-    // blocks of fewer rows to fill the GPU.
+    // Large blocks: 2 i per thread amortise the shared-memory loads over more
+    // pairs; 4 need 166-252 registers in the packed loop and lose occupancy
+    // (at N = 2^20: plain 1.20 vs 1.18, compensated 1.02 vs 0.97 Tpairs/s).
+    // Small blocks need more blocks of fewer rows to fill the GPU.
     if (threads == 0) threads = n_act >= 8192 ? 128 : 64;
     if (ipt == 0) {
         const int64_t per_wave = static_cast<int64_t>(sm_count) * 128 * 2;
-        ipt = n_act >= 4 * per_wave ? 4 : n_act >= 2 * per_wave ? 2 : 1;
+        ipt = n_act >= 2 * per_wave ? 2 : 1;
     }
     if (shape_index(threads, ipt) < 0) return NBODY_EINVAL;
     const int per = threads * ipt;
@@ -99,7 +100,7 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
 
 size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
 {
-    if (cfg.split <= 1) return 0;
+    if (cfg.split <= 1 || mode == kModeSorted) return 0;
     const size_t nc = is_ds(mode) ? 14 : 7;
     return static_cast<size_t>(cfg.split) * nc * static_cast<size_t>(n_act) * sizeof(float);
 }
@@ -109,6 +110,11 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
                          DevStatus *st, cudaStream_t s, int64_t *launches)
 {
     if (n_act <= 0) return cudaSuccess;
+    if (mode == kModeSorted) {
+        const cudaError_t e = force_sorted_launch(js, n, active, n_act, eps2, acc, jerk, pot, st, s);
+        if (e == cudaSuccess) ++*launches;
+        return e;
+    }
     const ForceConfig &c = cfg;
     ForceParams P;
     P.posm = js.posm;

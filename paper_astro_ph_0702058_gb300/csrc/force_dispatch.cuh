@@ -1,14 +1,11 @@
 // Launch and dispatch of the force kernels over the compiled launch shapes.
-// NB_PACKED selects the packed-FP32 pair loop (force_x2.cuh) instead of the
-// scalar one (force_impl.cuh) at build time.
+// The plain and compensated modes run the packed-FP32 pair loop
+// (force_x2.cuh); building with -DNB_PACKED=0 selects the scalar loop of
+// force_impl.cuh instead.  The summation-check mode always runs the scalar loop.
 #pragma once
 
 #include "force_impl.cuh"
 #include "force_x2.cuh"
-
-#ifndef NB_PACKED
-#define NB_PACKED 0
-#endif
 
 namespace nb {
 

@@ -18,6 +18,10 @@
 
 #include "force_impl.cuh"
 
+#ifndef NB_PACKED
+#define NB_PACKED 1
+#endif
+
 namespace nb {
 
 typedef unsigned long long f2_t;  // two packed floats {lo, hi}

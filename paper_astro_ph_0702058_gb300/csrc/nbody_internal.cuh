@@ -21,8 +21,10 @@ constexpr float kPadPosition = 1e15f;  // coordinate of the massless padding par
 constexpr int kModePlain = NBODY_MODE_PLAIN;
 constexpr int kModeComp = NBODY_MODE_COMP;
 constexpr int kModeCheck = NBODY_MODE_SUMCHECK;
+constexpr int kModeSorted = NBODY_MODE_SORTED;
+constexpr int64_t kSortedMaxN = 32768;  // sorted mode: all j terms of a row fit in shared memory
 // Modes that read the hi/lo position split and keep double-single sums.
-__host__ __device__ constexpr bool is_ds(int mode) { return mode != kModePlain; }
+__host__ __device__ constexpr bool is_ds(int mode) { return mode == kModeComp || mode == kModeCheck; }
 
 // Device-side status word of a context (written by kernels, read by the host).
 enum : unsigned {
@@ -83,6 +85,11 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
                          int64_t n_act, float eps2, const ForceConfig &cfg, double *acc,
                          double *jerk, double *pot, void *partials, DevStatus *st,
                          cudaStream_t s, int64_t *launches);
+
+// ---- force_sorted.cu ----
+// One block per active row; terms sorted by size and added in FP32 (n <= kSortedMaxN).
+cudaError_t force_sorted_launch(const JStream &js, int64_t n, const int32_t *active, int64_t n_act, float eps2,
+                                double *acc, double *jerk, double *pot, DevStatus *st, cudaStream_t s);
 
 // ---- integrator.cu ----
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, bool comp,

@@ -3,7 +3,8 @@ against the accuracy parameter eta = 0.1 / 2^k, for N = 1k (k = 0, 2, .., 8) and
 (k = 0, 2, 4).
 
 For each eta the same Plummer sphere is integrated in plain FP32, in the
-compensated mode and by the FP64 oracle (eps = 1/256, dt_max = 1/64,
+compensated mode, in the sorted-summation ablation (Sect. 6: forces added by size,
+smallest first; N = 1k only) and by the FP64 oracle (eps = 1/256, dt_max = 1/64,
 dt_min = 2^-26).  The paper reports that at large eta the GPU and the FP64
 reference agree (the error is the integrator's) and that at small eta the
 single-precision GPU stops improving.  The mechanism shows
@@ -53,9 +54,12 @@ def test_energy_error_against_eta(n, ks):
         eta = 0.1 * 2.0 ** -k
         dp, nbp = _gpu_de(m, x, v, eta, "plain")
         dc, _ = _gpu_de(m, x, v, eta, "comp")
+        ds, nbs = _gpu_de(m, x, v, eta, "sorted") if n <= 1024 else (float("nan"), 0)
         do, nbo = _oracle_de(m, x, v, eta)
-        rows.append({"n": n, "eta": eta, "plain": dp, "comp": dc, "oracle": do, "blocks_gpu": nbp, "blocks_oracle": nbo})
-        print(f"\nN={n} eta=0.1/2^{k}: |dE/E| plain {dp:.2e} comp {dc:.2e} oracle {do:.2e} blocks {nbp}/{nbo}")
+        rows.append({"n": n, "eta": eta, "plain": dp, "comp": dc, "sorted": ds, "oracle": do, "blocks_gpu": nbp,
+                     "blocks_sorted": nbs, "blocks_oracle": nbo})
+        print(f"\nN={n} eta=0.1/2^{k}: |dE/E| plain {dp:.2e} comp {dc:.2e} sorted {ds:.2e} oracle {do:.2e} "
+              f"blocks {nbp}/{nbs}/{nbo}")
     out = os.environ.get("NBODY_RESULTS_DIR")
     if out:
         os.makedirs(out, exist_ok=True)

@@ -1,4 +1,5 @@
-"""Pins of the summation-check oracle (orc_rsqrt_rn_f32, orc_force_fp32_terms).
+"""Pins of the summation-check and sorted-summation oracles (orc_rsqrt_rn_f32,
+orc_force_fp32_terms, orc_force_sorted_fp32).
 
 The correctly rounded reciprocal square root is checked against 60-digit decimal
 arithmetic, and the FP32-term sums against a brute-force reconstruction in exact
@@ -51,8 +52,9 @@ def test_rsqrt_rn_exact_powers():
         assert oracle.rsqrt_rn_f32(np.float32(4.0) ** k) == np.float32(2.0) ** -k
 
 
-def _terms_exact(m, x, v, eps2, i):
-    """Sums of the FP32 terms for particle i, each FP32 operation rounded from its exact value."""
+def _terms_exact(m, x, v, eps2, i, comp=True):
+    """The 7 lists of FP32 terms over j != i for particle i (as exact rationals), each FP32
+    operation rounded from its exact value; comp: dx from the hi/lo split, else from fl32(x)."""
     F = lambda a: Fraction(float(a))
     R = lambda fr: F(_fl32(fr))
     e2 = F(np.float32(eps2))
@@ -60,11 +62,14 @@ def _terms_exact(m, x, v, eps2, i):
     lo = (x - hi.astype(np.float64)).astype(np.float32)
     u = v.astype(np.float32)
     mu = m.astype(np.float32)
-    sums = [Fraction(0)] * 7
+    terms = [[] for _ in range(7)]
     for j in range(len(m)):
         if j == i:
             continue
-        dx = [R(R(F(hi[j, c]) - F(hi[i, c])) + R(F(lo[j, c]) - F(lo[i, c]))) for c in range(3)]
+        if comp:
+            dx = [R(R(F(hi[j, c]) - F(hi[i, c])) + R(F(lo[j, c]) - F(lo[i, c]))) for c in range(3)]
+        else:
+            dx = [R(F(hi[j, c]) - F(hi[i, c])) for c in range(3)]
         dv = [R(F(u[j, c]) - F(u[i, c])) for c in range(3)]
         r2 = R(dx[2] * dx[2] + R(dx[1] * dx[1] + R(dx[0] * dx[0] + e2)))
         rinv = F(_rsqrt_decimal(np.float32(float(r2))))
@@ -74,10 +79,10 @@ def _terms_exact(m, x, v, eps2, i):
         mr3 = R(mr * rinv2)
         w = R(3 * R(xv * rinv2))
         for c in range(3):
-            sums[c] += R(mr3 * dx[c])
-            sums[3 + c] += R(mr3 * R(-w * dx[c] + dv[c]))
-        sums[6] += -mr
-    return [float(s) for s in sums]
+            terms[c].append(R(mr3 * dx[c]))
+            terms[3 + c].append(R(mr3 * R(-w * dx[c] + dv[c])))
+        terms[6].append(-mr)
+    return terms
 
 
 def test_fp32_terms_match_exact_rational_reconstruction():
@@ -86,7 +91,7 @@ def test_fp32_terms_match_exact_rational_reconstruction():
     eps2 = (1.0 / 64) ** 2
     acc, jerk, pot = oracle.force_fp32_terms(m, x, v, eps2)
     for i in range(7):
-        ref = _terms_exact(m, x, v, eps2, i)
+        ref = [float(sum(t)) for t in _terms_exact(m, x, v, eps2, i)]
         got = list(acc[i]) + list(jerk[i]) + [pot[i]]
         for c in range(7):
             assert got[c] == pytest.approx(ref[c], rel=1e-15, abs=1e-300), (i, c)
@@ -103,3 +108,33 @@ def test_fp32_terms_close_to_fp64_force():
     rp = np.abs(p32 - p64) / np.abs(p64)
     assert np.median(ra) < 1e-6 and np.median(rk) < 1e-5 and np.max(rp) < 1e-6
     assert np.median(ra) > 1e-12  # they are FP32 terms, not FP64 ones
+
+
+def test_sorted_sums_match_rational_reconstruction_bit_for_bit():
+    """Sorted ablation: terms ordered by magnitude (ties by raw bits), added in FP32 from the
+    smallest; every addition rounded from its exact value."""
+    m, x, v = plummer_sphere(9, 23)
+    m = m * (1.0 + 0.1 * np.arange(9))  # unequal masses: no ties in magnitude by symmetry
+    eps2 = (1.0 / 64) ** 2
+    acc, jerk, pot = oracle.force_sorted_fp32(m, x, v, eps2)
+    bits = lambda f: int(np.array(np.float32(float(f)), dtype=np.float32).view(np.uint32))
+    for i in range(9):
+        got = list(acc[i]) + list(jerk[i]) + [pot[i]]
+        for c, ts in enumerate(_terms_exact(m, x, v, eps2, i, comp=False)):
+            order = sorted(ts, key=lambda t: (bits(t) & 0x7FFFFFFF, bits(t)))
+            s = Fraction(0)
+            for t in order:
+                s = Fraction(float(_fl32(s + t)))
+            assert got[c] == float(s), (i, c)
+
+
+def test_sorted_order_matters_and_stays_fp32_accurate():
+    """The sorted FP32 sum is a different rounding of the same terms as the unsorted one, and
+    stays within single-precision accuracy of the FP64 force."""
+    m, x, v = plummer_sphere(2048, 24)
+    eps2 = (1.0 / 256) ** 2
+    act = np.arange(0, 2048, 8, dtype=np.int32)
+    a_s, k_s, _ = oracle.force_sorted_fp32(m, x, v, eps2, act)
+    a_d, k_d, _ = oracle.force(m, x, v, eps2, act)
+    ra = np.linalg.norm(a_s - a_d, axis=1) / np.linalg.norm(a_d, axis=1)
+    assert np.median(ra) < 1e-6 and np.max(ra) < 1e-4
