@@ -429,6 +429,79 @@ def c2_sweep(args):
     print(json.dumps({"workload": "c2 force-only sweep", "n": n, "eps": 1.0 / 256, "rows": rows}), flush=True)
 
 
+def block_run(args):
+    """Free-running block steps: C3 (N = 2^20, seed 3, eps = 1e-3, to t = 1/64) or C2 (N = 65536,
+    seed 2, eps = 1/256, to t = 1), eta = 0.02, dt_max = 1/64, dt_min = 2^-26, both modes.  Reports
+    blocks, mean block size, pair-interactions/s over the run (host loop through the public
+    nbody_step, wall clock after a synchronised start) and the relative energy error."""
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import plummer_sphere
+    if args.workload == "c3-blocks":
+        n, seed, eps2, t_end = N_DEFAULT if args.n == N_DEFAULT else args.n, 3, 1e-6, 1.0 / 64
+    else:
+        n, seed, eps2, t_end = 65536, 2, (1.0 / 256) ** 2, 1.0
+    m, x, v = plummer_sphere(n, seed)
+    torch.cuda.set_device(0)
+    rows = []
+    for mode in args.modes.split(","):
+        t0 = time.perf_counter()
+        with Simulation(m, x, v, eps2, eta=0.02, lmin=6, lmax=26, mode=mode) as sim:
+            sim.sync()
+            t_init = time.perf_counter() - t0
+            e0 = sum(sim.energy())
+            p0 = sim.stats()["pairs"]
+            t1 = time.perf_counter()
+            blocks = sim.step(t_end)
+            sim.sync()
+            wall = time.perf_counter() - t1
+            st = sim.stats()
+            e1 = sum(sim.energy())
+        pairs = st["pairs"] - p0
+        rows.append({"mode": mode, "blocks": int(blocks), "mean_block": pairs / max(1, blocks) / (n - 1),
+                     "pairs": int(pairs), "wall_s": wall, "pairs_per_s": pairs / wall, "init_s": t_init,
+                     "energy_error": abs((e1 - e0) / e0), "below_dt_min": int(st["below_dt_min"])})
+    print(json.dumps({"workload": args.workload, "n": n, "eps2": eps2, "eta": 0.02, "t_end": t_end,
+                      "rows": rows}), flush=True)
+
+
+def diff_workload(args):
+    """C5: loss and gradient of a shared-step Hermite rollout (N = 4096 Plummer, seed 5,
+    eps = 1/128, 256 steps of 2^-9, checkpoints every 16 steps) through nbody_diff_rollout,
+    plain mode; 1 warm-up and 3 timed calls (the call waits for its result)."""
+    import numpy as np
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import MODES
+    from paper_astro_ph_0702058_gb300._lib import nbody_diff_rollout
+    from synthetic import plummer_sphere
+    n, steps, level, ck = 4096, 256, 9, 16
+    m, x, v = plummer_sphere(n, 5)
+    torch.cuda.set_device(0)
+    dm, dx, dv = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (m, x, v))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gx, gv, gm = torch.zeros_like(dx), torch.zeros_like(dv), torch.zeros_like(dm)
+    stream = torch.cuda.current_stream()
+    call = lambda: nbody_diff_rollout(n, dm, dx, dv, (1.0 / 128) ** 2, level, steps, ck, MODES["plain"],
+                                      loss, gx, gv, gm, stream)
+    call()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        call()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    # forward (steps + 1 forces), recomputed segments (steps forces), one force VJP per force
+    pair_passes = (steps + 1) + steps + (steps + 1)
+    print(json.dumps({"workload": "diff (C5)", "n": n, "steps": steps, "dt": 2.0 ** -level,
+                      "checkpoint_every": ck, "ms_per_gradient": t * 1e3, "gradients_per_s": 1.0 / t,
+                      "pair_passes": pair_passes, "pairs_per_s": pair_passes * n * (n - 1) / t,
+                      "loss": float(loss.item()), "grad_norm": float(torch.linalg.norm(gx).item())}), flush=True)
+
+
 def ensemble_workload(args):
     """C4: 512 independent Plummer clusters (sizes log-uniform in [256, 8192) from seed 4),
     eps = 1/256, eta = 0.02, integrated to t = 1/4 as one batched, graph-replayed run
@@ -492,9 +565,10 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
-    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep", "c3-blocks", "c2-blocks", "diff"], default="c3",
                     help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run; "
-                         "c2-sweep: force-only rates against the block size at N = 65536")
+                         "c2-sweep: force-only rates against the block size at N = 65536; c3-blocks / c2-blocks: "
+                         "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5)")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--ens-sample", type=int, default=32, help="clusters run one context each, for comparison")
     ap.add_argument("--ens-mode", default="comp")
@@ -507,6 +581,12 @@ def main(argv=None):
         return
     if args.workload == "c2-sweep":
         c2_sweep(args)
+        return
+    if args.workload in ("c3-blocks", "c2-blocks"):
+        block_run(args)
+        return
+    if args.workload == "diff":
+        diff_workload(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -72,12 +72,18 @@ enum {
                               double-single sums on its own (the production mode sums 64
                               terms in FP32 first).  Slower; nbody_force / nbody_step only
                               (not the ensemble or the no-alloc entry point).              */
-    NBODY_MODE_SORTED = 3  /* ablation of the accumulation order (Sect. 6 of the paper): the
+    NBODY_MODE_SORTED = 3, /* ablation of the accumulation order (Sect. 6 of the paper): the
                               plain-mode FP32 pair terms, formed with correctly rounded
                               operations in a fixed order, sorted by magnitude per row and
                               component and added in FP32 from the smallest.  One block per
                               active particle; n <= 32768 (NBODY_EINVAL above).  nbody_force /
                               nbody_step only.                                              */
+    NBODY_MODE_DS = 4      /* double-single pair arithmetic (~46 significant bits) on the
+                              FP32 pipe: positions, velocities and masses as hi/lo splits of
+                              the FP64 values, rsqrt seed plus one Newton step, every product
+                              and sum double-single.  About 1e-12 from the FP64 definition;
+                              roughly 10x the FP32 work of the compensated mode.  nbody_force /
+                              nbody_step / nbody_diff_rollout only.                        */
 };
 
 typedef struct nbody_ctx nbody_ctx; /* opaque; owns all of its device memory */
@@ -87,7 +93,7 @@ typedef struct {
     double eta_init;  /* nu of Eq. (initTimestep); <= 0 means "same as eta"               */
     int lmin;         /* dt_max = 2^-lmin (paper: 0.125, lmin = 3)                          */
     int lmax;         /* dt_min = 2^-lmax (paper: 2^-26, lmax = 26); 0 <= lmin <= lmax <= 40 */
-    int mode;         /* NBODY_MODE_PLAIN, _COMP, _SUMCHECK or _SORTED                       */
+    int mode;         /* NBODY_MODE_PLAIN, _COMP, _SUMCHECK, _SORTED or _DS                  */
     int strict;       /* nonzero: a step clamped at dt_min makes nbody_correct fail with
                          NBODY_EDTMIN (the step is still taken); zero: it is only counted */
     int i_block;      /* force tuning, 0 = automatic: i-particles per thread (1, 2 or 4)    */

@@ -9,7 +9,7 @@ by callers, for device memory and streams.
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBODY_MODE_SORTED, NBODY_MODE_SUMCHECK,
+from ._lib import (NBODY_MODE_COMP, NBODY_MODE_DS, NBODY_MODE_PLAIN, NBODY_MODE_SORTED, NBODY_MODE_SUMCHECK,
                    NBodyError,  # noqa: F401
                    nbody_diff_rollout,
                    nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
@@ -20,7 +20,7 @@ from ._lib import (NBODY_MODE_COMP, NBODY_MODE_PLAIN, NBODY_MODE_SORTED, NBODY_M
                    nbody_strerror, nbody_sync)
 
 MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP, "sumcheck": NBODY_MODE_SUMCHECK,
-         "sorted": NBODY_MODE_SORTED}
+         "sorted": NBODY_MODE_SORTED, "ds": NBODY_MODE_DS}
 
 
 class Simulation:

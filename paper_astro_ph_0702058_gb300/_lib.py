@@ -33,6 +33,7 @@ NBODY_MODE_PLAIN = 0
 NBODY_MODE_COMP = 1
 NBODY_MODE_SUMCHECK = 2
 NBODY_MODE_SORTED = 3
+NBODY_MODE_DS = 4
 
 # Every symbol include/nbody.h declares (checked by the tests against the header).
 EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",

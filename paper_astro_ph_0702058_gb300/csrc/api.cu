@@ -86,7 +86,7 @@ struct nbody_ctx {
     double *state = nullptr;  // 13 n doubles: m, x[3], v[3], a[3], k[3]
     int64_t *t = nullptr;
     int8_t *level = nullptr;
-    float4 *jbuf = nullptr;   // 3 n_pad float4: posm, vel, poslo
+    float4 *jbuf = nullptr;   // 4 n_pad float4: posm, vel, poslo, vello
     int32_t *act_force = nullptr, *act_corr = nullptr, *act_sched = nullptr;
     double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
     double *stage = nullptr;  // 6 n doubles: external forces / AoS staging
@@ -201,7 +201,7 @@ int force_internal(nbody_ctx *c, int64_t n_act)
     const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, cfg, n_act));
     if (rp != NBODY_OK) return rp;
     int64_t launches = 0;
-    NB_CUDA(force_launch(c->p.mode, c->J, c->n, c->act_force, n_act, static_cast<float>(c->eps2), cfg,
+    NB_CUDA(force_launch(c->p.mode, c->J, c->n, c->act_force, n_act, c->eps2, cfg,
                          c->f_acc, c->f_jerk, c->f_pot, c->partials, c->st, c->s, &launches),
             "force kernel launch");
     c->stats.kernel_launches += launches;
@@ -219,7 +219,7 @@ int predict_internal(nbody_ctx *c, int64_t tick)
     if (tick < c->t_max)
         return fail(NBODY_EINVAL, "prediction time %lld ticks is before a particle time %lld",
                     static_cast<long long>(tick), static_cast<long long>(c->t_max));
-    NB_CUDA(predict_launch(c->S, c->J, tick, c->p.lmax, is_ds(c->p.mode), c->s, &c->stats.kernel_launches),
+    NB_CUDA(predict_launch(c->S, c->J, tick, c->p.lmax, predict_lo_parts(c->p.mode), c->s, &c->stats.kernel_launches),
             "predictor launch");
     c->t_pred = tick;
     c->pred_valid = true;
@@ -262,7 +262,7 @@ int check_params(const nbody_params *p)
     if (p->lmin < 0 || p->lmax > 40 || p->lmin > p->lmax)
         return fail(NBODY_EINVAL, "need 0 <= lmin <= lmax <= 40 (got %d, %d)", p->lmin, p->lmax);
     if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP && p->mode != NBODY_MODE_SUMCHECK &&
-        p->mode != NBODY_MODE_SORTED)
+        p->mode != NBODY_MODE_SORTED && p->mode != NBODY_MODE_DS)
         return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
     if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256)
         return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128 or 256");
@@ -329,7 +329,7 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->state), 13 * nd * sizeof(double)), "state allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->t), nd * sizeof(int64_t)), "time allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->level), nd), "level allocation");
-    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->jbuf), 3 * static_cast<size_t>(c->n_pad) * sizeof(float4)),
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->jbuf), 4 * static_cast<size_t>(c->n_pad) * sizeof(float4)),
             "j-stream allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_force), nd * sizeof(int32_t)), "list allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_corr), nd * sizeof(int32_t)), "list allocation");
@@ -365,11 +365,12 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     c->J.posm = c->jbuf;
     c->J.vel = c->jbuf + c->n_pad;
     c->J.poslo = c->jbuf + 2 * c->n_pad;
+    c->J.vello = c->jbuf + 3 * c->n_pad;
     c->J.n_pad = c->n_pad;
 
     cudaStream_t s = c->s;
     int64_t *L = &c->stats.kernel_launches;
-    NB_INIT(cudaMemsetAsync(c->jbuf, 0, 3 * static_cast<size_t>(c->n_pad) * sizeof(float4), s), "memset");
+    NB_INIT(cudaMemsetAsync(c->jbuf, 0, 4 * static_cast<size_t>(c->n_pad) * sizeof(float4), s), "memset");
     NB_INIT(pad_jstream_launch(c->J, n, s, &c->stats.kernel_launches), "padding kernel");
     NB_INIT(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s), "memset");
     NB_INIT(cudaMemsetAsync(c->state + 7 * nd, 0, 6 * nd * sizeof(double), s), "memset");

@@ -34,13 +34,15 @@ int shape_index(int threads, int ipt)
 // every device this library runs on is the same sm_103 part).
 int occupancy(int mode, int threads, int ipt)
 {
-    static int cache[3][9];
-    static bool filled[3][9];
+    static int cache[5][9];
+    static bool filled[5][9];
     const int si = shape_index(threads, ipt);
-    if (si < 0 || mode < 0 || mode > 2) return 0;
+    if (si < 0 || mode < 0 || mode > 4) return 0;
     if (!filled[mode][si]) {
         cache[mode][si] = mode == kModeComp    ? force_occupancy_comp(threads, ipt)
                           : mode == kModeCheck ? force_occupancy_check(threads, ipt)
+                          : mode == kModeDS    ? force_occupancy_ds()
+                          : mode == kModeSorted ? 1
                                                : force_occupancy_plain(threads, ipt);
         filled[mode][si] = true;
     }
@@ -59,6 +61,10 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     // pairs; 4 need 166-252 registers in the packed loop and lose occupancy
     // (at N = 2^20: plain 1.20 vs 1.18, compensated 1.02 vs 0.97 Tpairs/s).
     // Small blocks need more blocks of fewer rows to fill the GPU.
+    if (mode == kModeDS) {  // one shape: 128 threads, one i each
+        threads = 128;
+        ipt = 1;
+    }
     if (threads == 0) threads = n_act >= 8192 ? 128 : 64;
     if (ipt == 0) {
         const int64_t per_wave = static_cast<int64_t>(sm_count) * 128 * 2;
@@ -101,15 +107,27 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
 size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
 {
     if (cfg.split <= 1 || mode == kModeSorted) return 0;
-    const size_t nc = is_ds(mode) ? 14 : 7;
+    const size_t nc = two_word_sums(mode) ? 14 : 7;
     return static_cast<size_t>(cfg.split) * nc * static_cast<size_t>(n_act) * sizeof(float);
 }
 
-cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active, int64_t n_act, float eps2,
+cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active, int64_t n_act, double eps2_d,
                          const ForceConfig &cfg, double *acc, double *jerk, double *pot, void *partials,
                          DevStatus *st, cudaStream_t s, int64_t *launches)
 {
     if (n_act <= 0) return cudaSuccess;
+    const float eps2 = static_cast<float>(eps2_d);
+    if (mode == kModeDS) {
+        cudaError_t e = force_ds_launch(js, n, active, n_act, eps2_d, cfg, acc, jerk, pot, partials, st, s);
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        if (cfg.split > 1) {
+            e = reduce_comp(static_cast<float *>(partials), cfg.split, static_cast<int>(n_act), acc, jerk, pot, s);
+            if (e != cudaSuccess) return e;
+            ++*launches;
+        }
+        return cudaSuccess;
+    }
     if (mode == kModeSorted) {
         const cudaError_t e = force_sorted_launch(js, n, active, n_act, eps2, acc, jerk, pot, st, s);
         if (e == cudaSuccess) ++*launches;

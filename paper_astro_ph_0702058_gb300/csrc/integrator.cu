@@ -21,7 +21,7 @@ int blocks_for(int64_t n, int threads, int cap = 1 << 20)
     return static_cast<int>(b < cap ? b : cap);
 }
 
-__global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int comp)
+__global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int lo_parts)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -32,12 +32,19 @@ __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, do
         const float hx = __double2float_rn(xp[0]);
         const float hy = __double2float_rn(xp[1]);
         const float hz = __double2float_rn(xp[2]);
-        J.posm[i] = make_float4(hx, hy, hz, __double2float_rn(S.m[i]));
-        J.vel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
-        if (comp)
+        const float hm = __double2float_rn(S.m[i]);
+        const float hvx = __double2float_rn(vp[0]), hvy = __double2float_rn(vp[1]), hvz = __double2float_rn(vp[2]);
+        J.posm[i] = make_float4(hx, hy, hz, hm);
+        J.vel[i] = make_float4(hvx, hvy, hvz, 0.f);
+        if (lo_parts)
             J.poslo[i] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
                                      __double2float_rn(xp[1] - static_cast<double>(hy)),
-                                     __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+                                     __double2float_rn(xp[2] - static_cast<double>(hz)),
+                                     lo_parts > 1 ? __double2float_rn(S.m[i] - static_cast<double>(hm)) : 0.f);
+        if (lo_parts > 1)
+            J.vello[i] = make_float4(__double2float_rn(vp[0] - static_cast<double>(hvx)),
+                                     __double2float_rn(vp[1] - static_cast<double>(hvy)),
+                                     __double2float_rn(vp[2] - static_cast<double>(hvz)), 0.f);
     }
 }
 
@@ -322,11 +329,11 @@ cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches
     return cudaGetLastError();
 }
 
-cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, bool comp,
+cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
                            cudaStream_t s, int64_t *launches)
 {
     predict_kernel<<<blocks_for(S.n, kThreads, 152 * 64), kThreads, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
-                                                                           comp ? 1 : 0);
+                                                                           lo_parts);
     ++*launches;
     return cudaGetLastError();
 }

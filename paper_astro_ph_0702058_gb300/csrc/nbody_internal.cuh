@@ -22,9 +22,15 @@ constexpr int kModePlain = NBODY_MODE_PLAIN;
 constexpr int kModeComp = NBODY_MODE_COMP;
 constexpr int kModeCheck = NBODY_MODE_SUMCHECK;
 constexpr int kModeSorted = NBODY_MODE_SORTED;
+constexpr int kModeDS = NBODY_MODE_DS;
 constexpr int64_t kSortedMaxN = 32768;  // sorted mode: all j terms of a row fit in shared memory
-// Modes that read the hi/lo position split and keep double-single sums.
+// Modes of force_kernel that read the hi/lo position split and keep double-single sums.
 __host__ __device__ constexpr bool is_ds(int mode) { return mode == kModeComp || mode == kModeCheck; }
+// Modes whose j-range partial sums are (hi, lo) pairs (14 floats per row).
+constexpr bool two_word_sums(int mode) { return is_ds(mode) || mode == kModeDS; }
+// What the predictor writes besides (x_hi, m_hi) and v_hi: 1 = position lo parts, 2 = also the
+// mass lo part (in poslo.w) and the velocity lo parts.
+constexpr int predict_lo_parts(int mode) { return mode == kModeDS ? 2 : is_ds(mode) ? 1 : 0; }
 
 // Device-side status word of a context (written by kernels, read by the host).
 enum : unsigned {
@@ -58,7 +64,8 @@ struct State {
 struct JStream {
     float4 *posm;   // (x_hi, y_hi, z_hi, m)
     float4 *vel;    // (vx, vy, vz, 0)
-    float4 *poslo;  // (x - x_hi, y - y_hi, z - z_hi, 0) rounded to float; compensated mode
+    float4 *poslo;  // (x - x_hi, y - y_hi, z - z_hi, m - m_hi) rounded to float; compensated (m part 0) and DS modes
+    float4 *vello;  // (vx - vx_hi, vy - vy_hi, vz - vz_hi, 0) rounded to float; DS mode
     int64_t n_pad;
 };
 
@@ -82,9 +89,15 @@ size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act);
 // Launches the force evaluation (and the fixed-order partial reduction when
 // split > 1).  acc/jerk: n_act*3, pot: n_act, device doubles.
 cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active,
-                         int64_t n_act, float eps2, const ForceConfig &cfg, double *acc,
+                         int64_t n_act, double eps2, const ForceConfig &cfg, double *acc,
                          double *jerk, double *pot, void *partials, DevStatus *st,
                          cudaStream_t s, int64_t *launches);
+
+// ---- force_ds.cu ----
+int force_occupancy_ds();
+cudaError_t force_ds_launch(const JStream &js, int64_t n, const int32_t *active, int64_t n_act, double eps2,
+                            const ForceConfig &cfg, double *acc, double *jerk, double *pot, void *partials,
+                            DevStatus *st, cudaStream_t s);
 
 // ---- force_sorted.cu ----
 // One block per active row; terms sorted by size and added in FP32 (n <= kSortedMaxN).
@@ -92,7 +105,7 @@ cudaError_t force_sorted_launch(const JStream &js, int64_t n, const int32_t *act
                                 double *acc, double *jerk, double *pot, DevStatus *st, cudaStream_t s);
 
 // ---- integrator.cu ----
-cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, bool comp,
+cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
                            cudaStream_t s, int64_t *launches);
 cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act,
                            const double *acc, const double *jerk, int64_t t_new, double eta,

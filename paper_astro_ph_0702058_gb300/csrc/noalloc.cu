@@ -134,9 +134,10 @@ extern "C" int nbody_force_noalloc(const float *posm, const float *vel, const fl
     js.posm = reinterpret_cast<float4 *>(const_cast<float *>(posm));
     js.vel = reinterpret_cast<float4 *>(const_cast<float *>(vel));
     js.poslo = reinterpret_cast<float4 *>(const_cast<float *>(mode == NBODY_MODE_COMP ? poslo : posm));
+    js.vello = nullptr;
     js.n_pad = n_pad;
     int64_t launches = 0;
-    e = force_launch(mode, js, n, active, n_act, static_cast<float>(eps2), cfg, acc, jerk, pot, A.partials,
+    e = force_launch(mode, js, n, active, n_act, eps2, cfg, acc, jerk, pot, A.partials,
                      A.status, s, &launches);
     if (e != cudaSuccess) return cuda_fail(e, "force kernel launch");
     DevStatus st;

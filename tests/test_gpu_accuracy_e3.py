@@ -4,15 +4,17 @@ against the accuracy parameter eta = 0.1 / 2^k, for N = 1k (k = 0, 2, .., 8) and
 
 For each eta the same Plummer sphere is integrated in plain FP32, in the
 compensated mode, in the sorted-summation ablation (Sect. 6: forces added by size,
-smallest first; N = 1k only) and by the FP64 oracle (eps = 1/256, dt_max = 1/64,
+smallest first; N = 1k only), with double-single pair arithmetic, and by the FP64 oracle (eps = 1/256, dt_max = 1/64,
 dt_min = 2^-26).  The paper reports that at large eta the GPU and the FP64
 reference agree (the error is the integrator's) and that at small eta the
 single-precision GPU stops improving.  The mechanism shows
 in the block counts: the corrector's a^(2) and a^(3) are force differences
 divided by dt^2 and dt^3, so at small steps the FP32 force noise dominates them,
 the Aarseth criterion shrinks the steps, and the FP32-force runs take many more
-blocks than the FP64 run.  The test checks agreement at large eta, the FP64
-error's fall with eta, and that growth of the block count, and prints the table
+blocks than the FP64 run.  The double-single run, whose forces are ~1e-12 from
+FP64, follows the oracle's block count and error at every eta.  The test checks
+agreement at large eta, the FP64 error's fall with eta, that growth of the block
+count, the double-single run's agreement, and prints the table
 (also written as JSON to $NBODY_RESULTS_DIR when that is set)."""
 import json
 import os
@@ -55,11 +57,12 @@ def test_energy_error_against_eta(n, ks):
         dp, nbp = _gpu_de(m, x, v, eta, "plain")
         dc, _ = _gpu_de(m, x, v, eta, "comp")
         ds, nbs = _gpu_de(m, x, v, eta, "sorted") if n <= 1024 else (float("nan"), 0)
+        dd, nbd = _gpu_de(m, x, v, eta, "ds")
         do, nbo = _oracle_de(m, x, v, eta)
-        rows.append({"n": n, "eta": eta, "plain": dp, "comp": dc, "sorted": ds, "oracle": do, "blocks_gpu": nbp,
-                     "blocks_sorted": nbs, "blocks_oracle": nbo})
-        print(f"\nN={n} eta=0.1/2^{k}: |dE/E| plain {dp:.2e} comp {dc:.2e} sorted {ds:.2e} oracle {do:.2e} "
-              f"blocks {nbp}/{nbs}/{nbo}")
+        rows.append({"n": n, "eta": eta, "plain": dp, "comp": dc, "sorted": ds, "ds": dd, "oracle": do,
+                     "blocks_gpu": nbp, "blocks_sorted": nbs, "blocks_ds": nbd, "blocks_oracle": nbo})
+        print(f"\nN={n} eta=0.1/2^{k}: |dE/E| plain {dp:.2e} comp {dc:.2e} sorted {ds:.2e} ds {dd:.2e} "
+              f"oracle {do:.2e} blocks plain/sorted/ds/oracle {nbp}/{nbs}/{nbd}/{nbo}")
     out = os.environ.get("NBODY_RESULTS_DIR")
     if out:
         os.makedirs(out, exist_ok=True)
@@ -74,4 +77,7 @@ def test_energy_error_against_eta(n, ks):
     # the same block schedule at large eta; at small eta FP32 forces make the criterion noisy
     assert big["blocks_gpu"] <= 1.05 * big["blocks_oracle"]
     assert small["blocks_gpu"] >= 2 * small["blocks_oracle"]
-    assert np.isfinite([r[k] for r in rows for k in ("plain", "comp", "oracle")]).all()
+    assert np.isfinite([r[k] for r in rows for k in ("plain", "comp", "ds", "oracle")]).all()
+    # double-single forces follow the FP64 oracle at every eta: no step collapse, same error
+    for r in rows:
+        assert r["blocks_ds"] <= 1.02 * r["blocks_oracle"] and 0.5 < r["ds"] / r["oracle"] < 2.0
