@@ -21,6 +21,11 @@
 #ifndef NB_PACKED
 #define NB_PACKED 1
 #endif
+// Register cap per thread for the packed kernels (0 = none): the launch
+// bounds then ask for 65536 / (NT * cap) resident blocks per SM.
+#ifndef NB_X2_REGCAP
+#define NB_X2_REGCAP 0
+#endif
 
 namespace nb {
 
@@ -159,8 +164,14 @@ __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j
     }
 }
 
+template <int NT>
+constexpr int x2_min_blocks()
+{
+    return NB_X2_REGCAP > 0 ? (65536 / (NT * NB_X2_REGCAP) > 0 ? 65536 / (NT * NB_X2_REGCAP) : 1) : 1;
+}
+
 template <int MODE, int NT, int IPT, int PF>
-__global__ void __launch_bounds__(NT) force_kernel_x2(const ForceParams P)
+__global__ void __launch_bounds__(NT, x2_min_blocks<NT>()) force_kernel_x2(const ForceParams P)
 {
     constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
