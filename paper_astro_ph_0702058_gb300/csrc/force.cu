@@ -57,19 +57,18 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     const int n_tiles = static_cast<int>(n_pad / kJTile);
     int threads = req_threads;
     int ipt = req_ipt;
-    // Large blocks: 2 i per thread amortise the shared-memory loads over more
-    // pairs; 4 need 166-252 registers in the packed loop and lose occupancy
-    // (at N = 2^20: plain 1.20 vs 1.18, compensated 1.02 vs 0.97 Tpairs/s).
-    // Small blocks need more blocks of fewer rows to fill the GPU.
+    // Packed loop: one i per thread keeps registers low (74 plain, 94
+    // compensated) and resident warps high, which beats amortising the shared
+    // loads over 2 or 4 i (134-252 registers).  At N = 2^20, in Tpairs/s:
+    // plain 1.26 (256 x 1), 1.24 (128 x 1), 1.23 (128 x 2), 1.22 (128 x 4);
+    // compensated 1.05, 1.03, 0.98, 0.97.  Small blocks take 64 threads so
+    // that more blocks of fewer rows fill the GPU.
     if (mode == kModeDS) {  // one shape: 128 threads, one i each
         threads = 128;
         ipt = 1;
     }
-    if (threads == 0) threads = n_act >= 8192 ? 128 : 64;
-    if (ipt == 0) {
-        const int64_t per_wave = static_cast<int64_t>(sm_count) * 128 * 2;
-        ipt = n_act >= 2 * per_wave ? 2 : 1;
-    }
+    if (threads == 0) threads = n_act >= 8192 ? 256 : 64;
+    if (ipt == 0) ipt = 1;
     if (shape_index(threads, ipt) < 0) return NBODY_EINVAL;
     const int per = threads * ipt;
     const int n_iblk = static_cast<int>(std::max<int64_t>(1, (n_act + per - 1) / per));

@@ -164,14 +164,14 @@ __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j
     }
 }
 
-template <int NT>
-constexpr int x2_min_blocks()
-{
-    return NB_X2_REGCAP > 0 ? (65536 / (NT * NB_X2_REGCAP) > 0 ? 65536 / (NT * NB_X2_REGCAP) : 1) : 1;
-}
+#if NB_X2_REGCAP > 0
+#define NB_X2_BOUNDS(NT) __launch_bounds__(NT, (65536 / ((NT) * NB_X2_REGCAP) > 0 ? 65536 / ((NT) * NB_X2_REGCAP) : 1))
+#else
+#define NB_X2_BOUNDS(NT) __launch_bounds__(NT)
+#endif
 
 template <int MODE, int NT, int IPT, int PF>
-__global__ void __launch_bounds__(NT, x2_min_blocks<NT>()) force_kernel_x2(const ForceParams P)
+__global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 {
     constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
