@@ -530,7 +530,7 @@ def ensemble_workload(args):
         ek, ep = ens.energy()
     pairs = int(st["pairs"].sum())
     # one context per cluster, each run by its own host loop (one launch sequence per block)
-    sample = list(range(0, n_cl, max(1, n_cl // args.ens_sample)))
+    sample = list(range(0, n_cl, max(1, n_cl // args.ens_sample))) if args.ens_sample > 0 else []
     t0 = time.perf_counter()
     single_pairs = 0
     for c in sample:
@@ -539,7 +539,7 @@ def ensemble_workload(args):
             sim.step(t_end)
             single_pairs += sim.stats()["pairs"] - len(mc) * (len(mc) - 1)  # without the t = 0 force
     single = time.perf_counter() - t0
-    per_cluster_s = single / len(sample)
+    per_cluster_s = single / len(sample) if sample else float("nan")
     out = {"workload": "ensemble", "clusters": n_cl, "particles": int(sizes.sum()), "mode": mode,
            "t_end": t_end, "batched_steps": int(steps), "blocks_total": int(st["blocks"].sum()),
            "wall_s": wall, "clusters_per_s": n_cl / wall, "pairs": pairs, "pairs_per_s": pairs / wall,
@@ -547,7 +547,7 @@ def ensemble_workload(args):
                            "ms_per_batched_step_in_tuning": shape[3]},
            "one_context_per_cluster": {"sample": len(sample), "s_per_cluster": per_cluster_s,
                                        "clusters_per_s": 1.0 / per_cluster_s,
-                                       "pairs_per_s": single_pairs / single},
+                                       "pairs_per_s": single_pairs / single if sample else None},
            "speedup_clusters_per_s": (n_cl / wall) * per_cluster_s,
            "energy_error_median": float(np.median(np.abs((ek + ep - e0) / e0))),
            "energy_error_max": float(np.max(np.abs((ek + ep - e0) / e0)))}
@@ -570,7 +570,8 @@ def main(argv=None):
                          "c2-sweep: force-only rates against the block size at N = 65536; c3-blocks / c2-blocks: "
                          "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5)")
     ap.add_argument("--clusters", type=int, default=512)
-    ap.add_argument("--ens-sample", type=int, default=32, help="clusters run one context each, for comparison")
+    ap.add_argument("--ens-sample", type=int, default=32,
+                    help="clusters run one context each, for comparison (0: skip the comparison)")
     ap.add_argument("--ens-mode", default="comp")
     args = ap.parse_args(argv)
     if args.force_only:
