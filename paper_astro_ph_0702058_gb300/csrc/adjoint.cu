@@ -23,10 +23,14 @@ namespace {
 constexpr int kVjpThreads = 128;
 constexpr int kVjpTile = 128;
 
+// grid (i-blocks, j-ranges): block (x, y) takes the particles p of i-block x
+// against the j-tiles of range y.  With one range it adds its totals to the
+// gradients; with several it writes them to part[y][7][n] and
+// vjp_reduce_kernel adds the ranges in ascending order (deterministic).
 __global__ void __launch_bounds__(kVjpThreads)
     force_vjp_kernel(const float4 *__restrict__ posm, const float4 *__restrict__ vel,
                      const float4 *__restrict__ gA, const float4 *__restrict__ gK, int n, int n_pad, float eps2,
-                     DiffGrads G)
+                     int tiles_per_range, double *__restrict__ part, DiffGrads G)
 {
     __shared__ float4 sp[kVjpTile], sv[kVjpTile], sa[kVjpTile], sk[kVjpTile];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,7 +38,9 @@ __global__ void __launch_bounds__(kVjpThreads)
     const float4 xi = posm[pl], vi = vel[pl], ga = gA[pl], gk = gK[pl];
     const float mp = xi.w;
     double tx[3] = {0, 0, 0}, tv[3] = {0, 0, 0}, tm = 0.0;
-    for (int j0 = 0; j0 < n_pad; j0 += kVjpTile) {
+    const int j_begin = blockIdx.y * tiles_per_range * kVjpTile;
+    const int j_end = min(j_begin + tiles_per_range * kVjpTile, n_pad);
+    for (int j0 = j_begin; j0 < j_end; j0 += kVjpTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kVjpTile; t += blockDim.x) {
             sp[t] = posm[j0 + t];
@@ -83,14 +89,43 @@ __global__ void __launch_bounds__(kVjpThreads)
         }
         tm += pm;
     }
-    if (p < n) {
+    if (p >= n) return;
+    if (gridDim.y == 1) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             G.gxp[c][p] += tx[c];
             G.gvp[c][p] += tv[c];
         }
         G.gm[p] += tm;
+    } else {
+        double *b = part + static_cast<size_t>(blockIdx.y) * 7 * n + p;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            b[static_cast<size_t>(c) * n] = tx[c];
+            b[static_cast<size_t>(3 + c) * n] = tv[c];
+        }
+        b[static_cast<size_t>(6) * n] = tm;
     }
+}
+
+__global__ void vjp_reduce_kernel(const double *__restrict__ part, int ranges, int n, DiffGrads G)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double t[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) t[c] = 0.0;
+    for (int y = 0; y < ranges; ++y) {
+        const double *b = part + static_cast<size_t>(y) * 7 * n + p;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) t[c] += b[static_cast<size_t>(c) * n];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        G.gxp[c][p] += t[c];
+        G.gvp[c][p] += t[3 + c];
+    }
+    G.gm[p] += t[6];
 }
 
 // Transposed corrector: from the gradients of the corrected state (gx, gv, ga,
@@ -220,13 +255,37 @@ int blocks_of(int64_t n, int t) { return static_cast<int>((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, float eps2, cudaStream_t s,
-                             int64_t *launches)
+int vjp_ranges(int64_t n, int64_t n_pad, int sm_count)
 {
-    force_vjp_kernel<<<blocks_of(n, kVjpThreads), kVjpThreads, 0, s>>>(J.posm, J.vel, G.gA, G.gK,
-                                                                      static_cast<int>(n),
-                                                                      static_cast<int>(J.n_pad), eps2, G);
+    // enough blocks for about four per SM; ranges of whole tiles
+    const int bx = blocks_of(n, kVjpThreads);
+    const int tiles = static_cast<int>(n_pad / kVjpTile);
+    const int want = (4 * sm_count + bx - 1) / bx;
+    const int r = want < 1 ? 1 : (want > tiles ? tiles : want);
+    const int tpr = (tiles + r - 1) / r;
+    return (tiles + tpr - 1) / tpr;
+}
+
+size_t vjp_scratch_doubles(int64_t n, int64_t n_pad, int sm_count)
+{
+    const int r = vjp_ranges(n, n_pad, sm_count);
+    return r > 1 ? static_cast<size_t>(r) * 7 * static_cast<size_t>(n) : 0;
+}
+
+cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, float eps2, int sm_count,
+                             double *scratch, cudaStream_t s, int64_t *launches)
+{
+    const int tiles = static_cast<int>(J.n_pad / kVjpTile);
+    const int r = vjp_ranges(n, J.n_pad, sm_count);
+    const int tpr = (tiles + r - 1) / r;
+    const dim3 grid(blocks_of(n, kVjpThreads), r);
+    force_vjp_kernel<<<grid, kVjpThreads, 0, s>>>(J.posm, J.vel, G.gA, G.gK, static_cast<int>(n),
+                                                  static_cast<int>(J.n_pad), eps2, tpr, scratch, G);
     ++*launches;
+    if (r > 1) {
+        vjp_reduce_kernel<<<blocks_of(n, 256), 256, 0, s>>>(scratch, r, static_cast<int>(n), G);
+        ++*launches;
+    }
     return cudaGetLastError();
 }
 

@@ -636,7 +636,7 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
     const size_t npad = static_cast<size_t>(c->n_pad);
     const int64_t n_ck = steps / checkpoint_every + 1;
     const size_t state_doubles = 12 * nd;  // x, v, a, k (contiguous after m)
-    double *ck = nullptr, *seg = nullptr, *gbuf = nullptr, *lval = nullptr, *dloss = nullptr;
+    double *ck = nullptr, *seg = nullptr, *gbuf = nullptr, *lval = nullptr, *dloss = nullptr, *vjp = nullptr;
     float4 *g4 = nullptr;
     DiffGrads G{};
     const double dt = std::ldexp(1.0, -level);
@@ -645,7 +645,7 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
     int64_t *L = &c->stats.kernel_launches;
     auto done = [&](int code) {
         cudaStreamSynchronize(s);
-        void *bufs[] = {ck, seg, gbuf, lval, dloss, g4};
+        void *bufs[] = {ck, seg, gbuf, lval, dloss, g4, vjp};
         for (void *b : bufs)
             if (b) cudaFree(b);
         nbody_free(c);
@@ -662,6 +662,8 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
     NB_DR(dev_alloc(reinterpret_cast<void **>(&lval), nd * sizeof(double)), "loss terms");
     NB_DR(dev_alloc(reinterpret_cast<void **>(&dloss), sizeof(double)), "loss");
     NB_DR(dev_alloc(reinterpret_cast<void **>(&g4), 2 * npad * sizeof(float4)), "force upstream");
+    const size_t vjp_doubles = vjp_scratch_doubles(n, c->n_pad, c->sm_count);
+    if (vjp_doubles) NB_DR(dev_alloc(reinterpret_cast<void **>(&vjp), vjp_doubles * sizeof(double)), "adjoint scratch");
     NB_DR(cudaMemsetAsync(gbuf, 0, 19 * nd * sizeof(double), s), "memset");
     NB_DR(cudaMemsetAsync(g4, 0, 2 * npad * sizeof(float4), s), "memset");
     for (int q = 0; q < 3; ++q) {
@@ -723,7 +725,7 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
             r = predict_internal(c, k + 1);  // j-stream at the predicted state of step k
             if (r != NBODY_OK) return done(r);
             NB_DR(adj_correct_launch(G, n, dt, s, L), "adjoint corrector");
-            NB_DR(force_vjp_launch(c->J, G, n, e2, s, L), "force adjoint");
+            NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
             NB_DR(adj_predict_launch(G, n, dt, s, L), "adjoint predictor");
         }
     }
@@ -733,7 +735,7 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
     r = predict_internal(c, 0);
     if (r != NBODY_OK) return done(r);
     NB_DR(adj_init_launch(G, n, s, L), "adjoint init");
-    NB_DR(force_vjp_launch(c->J, G, n, e2, s, L), "force adjoint");
+    NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
     NB_DR(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDefault, s), "loss copy");
     NB_DR(soa_to_aos_launch(G.gxp[0], G.gxp[1], G.gxp[2], c->stage, n, s, L), "layout");
     NB_DR(cudaMemcpyAsync(g_x0, c->stage, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");

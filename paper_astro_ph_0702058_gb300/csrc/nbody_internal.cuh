@@ -143,8 +143,10 @@ struct DiffGrads {
     double *gm;                             // gradient of the masses
     float4 *gA, *gK;                        // upstream of the force (n_pad, zero padded)
 };
-cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, float eps2, cudaStream_t s,
-                             int64_t *launches);
+// Doubles of scratch the force VJP needs for its j-range partial sums (0: none).
+size_t vjp_scratch_doubles(int64_t n, int64_t n_pad, int sm_count);
+cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, float eps2, int sm_count,
+                             double *scratch, cudaStream_t s, int64_t *launches);
 cudaError_t adj_correct_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches);
 cudaError_t adj_predict_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches);
 cudaError_t adj_init_launch(const DiffGrads &G, int64_t n, cudaStream_t s, int64_t *launches);
