@@ -26,6 +26,12 @@
 #ifndef NB_X2_REGCAP
 #define NB_X2_REGCAP 0
 #endif
+// Unroll factor of the packed loop over groups of 4 j.
+#ifndef NB_X2_UNROLL
+#define NB_X2_UNROLL 2
+#endif
+#define NB_PRAGMA(x) _Pragma(#x)
+#define NB_UNROLL(n) NB_PRAGMA(unroll n)
 
 namespace nb {
 
@@ -130,7 +136,7 @@ __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j
         for (int u = 0; u < IPT; ++u)
 #pragma unroll
             for (int c = 0; c < 7; ++c) p[u][c] = 0ull;
-#pragma unroll 2
+NB_UNROLL(NB_X2_UNROLL)
         for (int jj = 0; jj < PF; jj += 4) {
             f2_t v[SoaTile<MODE>::NA][2];
 #pragma unroll
