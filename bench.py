@@ -244,9 +244,18 @@ def cpu_baseline(m, x, v, n, target_s=12.0):
     fa, fk, _ = oracle.force(m, xp, vp, EPS2, act)
     st.correct(act, xp, vp, fa, fk, t_new)
     dt = time.perf_counter() - t0
-    return {"value": rows * (n - 1) / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"one step (predict all {n}, force on {rows} evenly spaced rows against all {n}, "
-                      f"correct those rows) in FP64, {dt:.1f} s"}
+    out = {"value": rows * (n - 1) / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+           "sample": f"one step (predict all {n}, force on {rows} evenly spaced rows against all {n}, "
+                     f"correct those rows) in FP64, {dt:.1f} s"}
+    # the same oracle force on one thread, on a smaller sample of rows
+    oracle.set_threads(1)
+    rows1 = max(8, rows // max(1, cores))
+    t0 = time.perf_counter()
+    oracle.force(m, xp, vp, EPS2, np.linspace(0, n - 1, rows1).astype(np.int32))
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    out["single_thread"] = {"value": rows1 * (n - 1) / dt1, "sample": f"force on {rows1} rows, {dt1:.1f} s"}
+    return out
 
 
 def bench_ours(args):
