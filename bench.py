@@ -511,6 +511,21 @@ def diff_workload(args):
                       "loss": float(loss.item()), "grad_norm": float(torch.linalg.norm(gx).item())}), flush=True)
 
 
+def pipe_probe(args):
+    """The roofline's unit rates, measured: FP32 FMA / ADD / MUL, packed FP32x2 FMA and MUFU rsqrt
+    results per SM per clock (csrc/pipe_probe.cu, chains of independent accumulators)."""
+    from paper_astro_ph_0702058_gb300 import build as nb_build
+    exe = nb_build.build_probe()
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    line = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else "{}"
+    out = {"workload": "pipe-probe", "rc": r.returncode}
+    try:
+        out.update(json.loads(line))
+    except ValueError:
+        out["raw"] = line
+    print(json.dumps(out), flush=True)
+
+
 def ensemble_workload(args):
     """C4: 512 independent Plummer clusters (sizes log-uniform in [256, 8192) from seed 4),
     eps = 1/256, eta = 0.02, integrated to t = 1/4 as one batched, graph-replayed run
@@ -574,10 +589,11 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
-    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep", "c3-blocks", "c2-blocks", "diff"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep", "c3-blocks", "c2-blocks", "diff", "pipe-probe"], default="c3",
                     help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run; "
                          "c2-sweep: force-only rates against the block size at N = 65536; c3-blocks / c2-blocks: "
-                         "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5)")
+                         "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5); "
+                         "pipe-probe: FP32 / FP32x2 / MUFU unit rates")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--ens-sample", type=int, default=32,
                     help="clusters run one context each, for comparison (0: skip the comparison)")
@@ -597,6 +613,9 @@ def main(argv=None):
         return
     if args.workload == "diff":
         diff_workload(args)
+        return
+    if args.workload == "pipe-probe":
+        pipe_probe(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -81,3 +81,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+
+
+def build_probe(out: str | None = None) -> str:
+    """Compiles the standalone pipe-throughput probe (csrc/pipe_probe.cu); returns its path."""
+    exe = out or os.path.join(BUILD, "pipe_probe")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    cmd = [nvcc(), os.path.join(CSRC, "pipe_probe.cu"), "-o", exe, "-O3", "-std=c++17"] + ARCH
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed on pipe_probe.cu")
+    return exe

@@ -94,11 +94,13 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     }
     split = std::max(1, std::min(split, n_tiles));
     if (req_split <= 0) {
-        // More, shorter blocks balance the SMs better at the end of a launch
-        // (measured +0.5-2 % up to about 12 waves); the partial sums cost
-        // 28-56 bytes per row and range.
+        // More, shorter blocks balance the SMs better at the end of a launch:
+        // +0.5-2 % for full forces, 10-20 % for blocks of 1k-2k rows at
+        // N = 65536, up to about 12 waves.  The partial sums cost 28-56 bytes
+        // per row and range, at most 12 x slots x threads x 56 bytes (~80 MB).
         const int slots = sm_count * std::max(1, occupancy(mode, threads, ipt));
-        while (split < n_tiles && split < 64 && static_cast<int64_t>(n_iblk) * split < 12LL * slots) ++split;
+        const int64_t want = (12LL * slots + n_iblk - 1) / n_iblk;
+        if (want > split) split = static_cast<int>(std::min<int64_t>(want, n_tiles));
     }
     const int tps = (n_tiles + split - 1) / split;
     split = (n_tiles + tps - 1) / tps;
