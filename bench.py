@@ -442,7 +442,8 @@ def block_run(args):
     """Free-running block steps: C3 (N = 2^20, seed 3, eps = 1e-3, to t = 1/64) or C2 (N = 65536,
     seed 2, eps = 1/256, to t = 1), eta = 0.02, dt_max = 1/64, dt_min = 2^-26, both modes.  Reports
     blocks, mean block size, pair-interactions/s over the run (host loop through the public
-    nbody_step, wall clock after a synchronised start) and the relative energy error."""
+    nbody_step, wall clock after a synchronised start) and the relative energy error.  C2 also runs the
+    double-single mode, whose drift stands in for the FP64 oracle's at this length."""
     import torch
 
     from paper_astro_ph_0702058_gb300 import Simulation
@@ -454,7 +455,10 @@ def block_run(args):
     m, x, v = plummer_sphere(n, seed)
     torch.cuda.set_device(0)
     rows = []
-    for mode in args.modes.split(","):
+    modes = args.modes.split(",")
+    if args.workload == "c2-blocks" and args.modes == "plain,comp":
+        modes.append("ds")  # double-single forces: the FP64-equivalent drift to compare with (C2 is too long for the CPU oracle)
+    for mode in modes:
         t0 = time.perf_counter()
         with Simulation(m, x, v, eps2, eta=0.02, lmin=6, lmax=26, mode=mode) as sim:
             sim.sync()
