@@ -435,7 +435,57 @@ def c2_sweep(args):
                 rows.append({"mode": mode, "n_act": n_act, "us": t * 1e6, "interactions_per_s": n_act * (n - 1) / t,
                              "threads": st["last_threads"], "i_block": st["last_i_per_thread"],
                              "j_split": st["last_j_split"]})
-    print(json.dumps({"workload": "c2 force-only sweep", "n": n, "eps": 1.0 / 256, "rows": rows}), flush=True)
+    # cpu_baseline leg: the FP64 oracle on the same inputs (all host cores, then one), 1594 sampled rows
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    act = active_subset(n, 1594, 2)
+    orc = {}
+    for threads in (cores, 1):
+        oracle.set_threads(threads)
+        rows_t = act if threads == cores else act[:max(16, 1594 // cores)]
+        t0 = time.perf_counter()
+        oracle.force(m, x, v, eps2, rows_t)
+        orc[f"threads_{threads}"] = len(rows_t) * (n - 1) / (time.perf_counter() - t0)
+    oracle.set_threads(cores)
+    print(json.dumps({"workload": "c2 force-only sweep", "n": n, "eps": 1.0 / 256, "rows": rows,
+                      "cpu_baseline": {"kind": "oracle", "interactions_per_s": orc,
+                                       "sample": "1594 sampled rows (n_act = 1594 set) against all N, FP64"}}),
+          flush=True)
+
+
+def c1_run(args):
+    """C1: N = 1024 Plummer (seed 1), eps = 1/256, eta = 0.01, dt_max = 1/64, dt_min = 2^-26, from t = 0 to
+    1/8, in every force mode and in the FP64 oracle: blocks, wall time and |dE/E|."""
+    import torch
+
+    import oracle
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import plummer_sphere
+    n, eps2, t_end = 1024, (1.0 / 256) ** 2, 0.125
+    m, x, v = plummer_sphere(n, 1)
+    torch.cuda.set_device(0)
+    rows = []
+    for mode in ("plain", "comp", "sorted", "ds"):
+        with Simulation(m, x, v, eps2, eta=0.01, lmin=6, lmax=26, mode=mode) as sim:
+            e0 = sum(sim.energy())
+            sim.sync()
+            t0 = time.perf_counter()
+            blocks = sim.step(t_end)
+            sim.sync()
+            wall = time.perf_counter() - t0
+            e1 = sum(sim.energy())
+        rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "energy_error": abs((e1 - e0) / e0)})
+    # cpu_baseline leg: the FP64 oracle's own run of C1 on the host cores
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    st = oracle.State(m, x, v, eps2, 0.01, lmin=6, lmax=26).init()
+    e0 = sum(st.energy())
+    t0 = time.perf_counter()
+    bt, _, _ = st.evolve(int(t_end * 2 ** 26))
+    wall = time.perf_counter() - t0
+    base = {"kind": "oracle", "blocks": len(bt), "wall_s": wall, "cores": oracle.get_threads(),
+            "energy_error": abs((sum(st.energy()) - e0) / e0), "sample": "the whole C1 run, FP64"}
+    print(json.dumps({"workload": "c1", "n": n, "eps2": eps2, "eta": 0.01, "t_end": t_end, "rows": rows,
+                      "cpu_baseline": base}), flush=True)
 
 
 def block_run(args):
@@ -593,11 +643,11 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
-    ap.add_argument("--workload", choices=["c3", "ensemble", "c2-sweep", "c3-blocks", "c2-blocks", "diff", "pipe-probe"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "ensemble", "c1", "c2-sweep", "c3-blocks", "c2-blocks", "diff", "pipe-probe"], default="c3",
                     help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run; "
                          "c2-sweep: force-only rates against the block size at N = 65536; c3-blocks / c2-blocks: "
                          "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5); "
-                         "pipe-probe: FP32 / FP32x2 / MUFU unit rates")
+                         "pipe-probe: FP32 / FP32x2 / MUFU unit rates; c1: the C1 run in every mode and the oracle")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--ens-sample", type=int, default=32,
                     help="clusters run one context each, for comparison (0: skip the comparison)")
@@ -620,6 +670,9 @@ def main(argv=None):
         return
     if args.workload == "pipe-probe":
         pipe_probe(args)
+        return
+    if args.workload == "c1":
+        c1_run(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
