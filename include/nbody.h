@@ -96,9 +96,11 @@ typedef struct {
     int mode;         /* NBODY_MODE_PLAIN, _COMP, _SUMCHECK, _SORTED or _DS                  */
     int strict;       /* nonzero: a step clamped at dt_min makes nbody_correct fail with
                          NBODY_EDTMIN (the step is still taken); zero: it is only counted */
-    int i_block;      /* force tuning, 0 = automatic: i-particles per thread (1, 2 or 4)    */
-    int j_tile;       /* force tuning, 0 = automatic: threads per block (64, 128 or 256)    */
-    int j_split;      /* force tuning, 0 = automatic: number of j-ranges (>= 1)             */
+    int i_block;      /* force tuning, 0 = automatic (1): i-particles per thread (1, 2, 4)  */
+    int j_tile;       /* force tuning, 0 = automatic (256 for blocks of >= 8192 rows, else
+                         64): threads per block (64, 128 or 256)                           */
+    int j_split;      /* force tuning, 0 = automatic (about 12 waves of blocks): number of
+                         j-ranges (>= 1); the double-single mode always takes 128 x 1     */
     void *stream;     /* cudaStream_t for all work of the context, or NULL                  */
 } nbody_params;
 
@@ -195,9 +197,11 @@ int nbody_set_state(nbody_ctx *ctx, const double *x, const double *v, const doub
 
 /* Copies the predicted j-stream of the last nbody_predict into caller
  * buffers (host or device; any may be NULL), n x 4 floats each:
- * posm = (x_hi, y_hi, z_hi, m), vel = (vx, vy, vz, 0) and, in compensated
- * mode, poslo = (x - x_hi, y - y_hi, z - z_hi, 0) rounded to float (zeros in
- * plain mode).  Synchronises the stream.  Errors: ESTATE (no prediction). */
+ * posm = (x_hi, y_hi, z_hi, m_hi), vel = (vx_hi, vy_hi, vz_hi, 0) and, in the
+ * compensated, summation-check and double-single modes, poslo = (x - x_hi,
+ * y - y_hi, z - z_hi, m - m_hi) rounded to float (the mass part only in the
+ * double-single mode; zeros in the plain and sorted modes).  Synchronises the
+ * stream.  Errors: ESTATE (no prediction). */
 int nbody_get_predicted(nbody_ctx *ctx, float *posm, float *vel, float *poslo);
 
 /* Counters of the context since nbody_init. */
