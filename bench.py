@@ -181,15 +181,16 @@ def run_steps(sim, n, steps, warmup, stream, flush, host=None):
     return total, [a.elapsed_time(b) for a, b in force_ms], launches
 
 
+# the force kernel's code; its launch shape is recorded and compared separately
 KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_astro_ph_0702058_gb300/csrc/ptx.cuh",
-                  "paper_astro_ph_0702058_gb300/csrc/force.cu", "paper_astro_ph_0702058_gb300/csrc/force_x2.cuh",
+                  "paper_astro_ph_0702058_gb300/csrc/force_x2.cuh",
                   "paper_astro_ph_0702058_gb300/csrc/force_dispatch.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic_n1048576.json")
 
 
-def measured_traffic(mode, n):
+def measured_traffic(mode, n, launch=None):
     """DRAM bytes per force launch from the committed ncu capture, or None when that
-    capture was of another size or the kernel source has changed since."""
+    capture was of another size or launch shape, or the kernel source has changed since."""
     import hashlib
     try:
         with open(TRAFFIC_FILE) as f:
@@ -202,16 +203,18 @@ def measured_traffic(mode, n):
             h.update(f.read())
     if rec.get("source_sha256") != h.hexdigest() or rec.get("n") != n or mode not in rec:
         return None
+    if launch is not None and list(rec[mode].get("launch", [])) != list(launch):
+        return None
     return rec[mode]["dram_read_bytes"] + rec[mode]["dram_write_bytes"]
 
 
-def roofline(force_ms_avg, n, sm_count, clocks, peaks, mode="comp"):
+def roofline(force_ms_avg, n, sm_count, clocks, peaks, mode="comp", launch=None):
     max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     pairs = n * (n - 1)
     achieved = pairs / (force_ms_avg * 1e-3) / 1e9
     peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / OPS_PER_PAIR / 1e9
     out = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Gpair/s",
-           "frac": round(achieved / peak, 4), "traffic": measured_traffic(mode, n),
+           "frac": round(achieved / peak, 4), "traffic": measured_traffic(mode, n, launch),
            "traffic_unit": "bytes per launch (ncu dram read + write)",
            "peak_basis": f"{sm_count} SM x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz / "
                          f"{OPS_PER_PAIR} FP32 ops per pair (derived from unit counts and the max SM clock)"}
@@ -291,7 +294,8 @@ def bench_ours(args):
             res[mode] = {"value": pairs_all / (t_max * 1e-3), "ms_per_step": t_max / args.steps,
                          "force_ms": statistics.mean(force_ms), "launches": launches, "clocks": clocks,
                          "wall_s": wall, "shape": f"{cfg['last_threads']} threads x {cfg['last_i_per_thread']} "
-                                                  f"i/thread, j-split {cfg['last_j_split']}"}
+                                                  f"i/thread, j-split {cfg['last_j_split']}",
+                         "launch": [cfg["last_threads"], cfg["last_i_per_thread"], cfg["last_j_split"]]}
         # end to end: pinned host list in/out and forces back to the host every step
         sim = make_sim(m, x, v, "comp", stream)
         host = (torch.zeros(n, dtype=torch.int32).pin_memory(), torch.zeros((n, 3), dtype=torch.float64).pin_memory(),
@@ -304,8 +308,8 @@ def bench_ours(args):
     if rank == 0:
         c = res["comp"]
         p = res["plain"]
-        rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks, "comp")
-        rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks, "plain")
+        rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks, "comp", c["launch"])
+        rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks, "plain", p["launch"])
         out = {
             "metric": METRIC, "value": c["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": c["ms_per_step"], "higher_is_better": True,
