@@ -26,9 +26,14 @@
 #ifndef NB_X2_REGCAP
 #define NB_X2_REGCAP 0
 #endif
-// Unroll factor of the packed loop over groups of 4 j.
+// Unroll factor of the packed loop over groups of NB_X2_JSTEP j, and the
+// group size: 4 (one 128-bit shared load per array gives two packed pairs)
+// or 2 (one 64-bit load, half the registers for staged j).
 #ifndef NB_X2_UNROLL
 #define NB_X2_UNROLL 2
+#endif
+#ifndef NB_X2_JSTEP
+#define NB_X2_JSTEP 4
 #endif
 #define NB_PRAGMA(x) _Pragma(#x)
 #define NB_UNROLL(n) NB_PRAGMA(unroll n)
@@ -136,17 +141,23 @@ __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j
         for (int u = 0; u < IPT; ++u)
 #pragma unroll
             for (int c = 0; c < 7; ++c) p[u][c] = 0ull;
+        constexpr int JS = NB_X2_JSTEP;
+        static_assert(JS == 2 || JS == 4, "j group of 2 or 4");
 NB_UNROLL(NB_X2_UNROLL)
-        for (int jj = 0; jj < PF; jj += 4) {
-            f2_t v[SoaTile<MODE>::NA][2];
+        for (int jj = 0; jj < PF; jj += JS) {
+            f2_t v[SoaTile<MODE>::NA][JS / 2];
 #pragma unroll
             for (int a = 0; a < SoaTile<MODE>::NA; ++a) {
-                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&T.a[a][jb + jj]);
-                v[a][0] = q.x;
-                v[a][1] = q.y;
+                if constexpr (JS == 4) {
+                    const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&T.a[a][jb + jj]);
+                    v[a][0] = q.x;
+                    v[a][JS / 2 - 1] = q.y;
+                } else {
+                    v[a][0] = *reinterpret_cast<const f2_t *>(&T.a[a][jb + jj]);
+                }
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < JS / 2; ++h)
 #pragma unroll
                 for (int u = 0; u < IPT; ++u)
                     pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
