@@ -63,3 +63,30 @@ def test_autograd_function():
     np.testing.assert_array_equal(xt.grad.cpu().numpy(), 3.0 * gx)
     np.testing.assert_array_equal(vt.grad.cpu().numpy(), 3.0 * gv)
     np.testing.assert_array_equal(mt.grad.cpu().numpy(), 3.0 * gm)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_size_gradient_against_double_single_finite_differences(mode):
+    """C5 at full size (N = 4096, eps = 1/128, 256 steps of 1/512, checkpoints every 16): the
+    directional derivative g . d of the adjoint gradient against central differences of the loss
+    computed with double-single forces (~1e-12 from FP64), along seeded directions in x0, v0 and m."""
+    need_gpu()
+    from paper_astro_ph_0702058_gb300 import MODES
+    n = 4096
+    m, x, v = plummer_sphere(n, 5)
+    L, gx, gv, gm = _gpu_grad(m, x, v, mode=mode)
+    rng = np.random.default_rng(17)
+    ds = MODES["ds"]
+    for what in ("x", "v", "m"):
+        d = rng.standard_normal((n, 3) if what != "m" else n)
+        if what == "m":
+            d *= m  # relative mass perturbations
+        h = 1e-4  # large enough to beat the double-single rounding noise, small against the curvature
+        args = {"x": x, "v": v, "m": m}
+        lp = _gpu_grad(*(args[k] + h * d if k == what else args[k] for k in ("m", "x", "v")), mode=ds)[0]
+        lm = _gpu_grad(*(args[k] - h * d if k == what else args[k] for k in ("m", "x", "v")), mode=ds)[0]
+        fd = (lp - lm) / (2 * h)
+        g = {"x": gx, "v": gv, "m": gm}[what]
+        an = float((g * d).sum())
+        print(f"\nmode {mode} d{what}: adjoint {an:.8e} finite difference {fd:.8e} rel {abs(an - fd) / abs(fd):.2e}")
+        assert abs(an - fd) <= 1e-3 * abs(fd)
