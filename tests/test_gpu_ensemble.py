@@ -103,3 +103,41 @@ def test_tuner_picks_a_shape_and_keeps_the_state():
         ek, ep = ens.energy()
     assert np.all(end["t_tick"] == int(T_END * 2 ** 26))
     assert np.all(np.isfinite(ek + ep))
+
+
+@pytest.mark.parametrize("mode", ["plain", "comp"])
+def test_full_size_c4_sampled_clusters(mode):
+    """C4 at full size (512 clusters, sizes from seed 4, 1,177,044 particles): the t = 0 forces and
+    energies of 8 sampled clusters against the oracle, then a tuned, graph-replayed run to t = 1/64
+    in which every cluster arrives and conserves energy to 1e-6."""
+    need_gpu()
+    from paper_astro_ph_0702058_gb300 import Ensemble
+    from synthetic import ensemble_sizes
+    sizes = ensemble_sizes(512, 4)
+    assert int(sizes.sum()) == 1177044
+    parts = [plummer_sphere(int(n), 4_000_000 + c) for c, n in enumerate(sizes)]
+    m = np.concatenate([p[0] for p in parts])
+    x = np.concatenate([p[1] for p in parts])
+    v = np.concatenate([p[2] for p in parts])
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    sample = np.linspace(0, 511, 8).astype(int)
+    with Ensemble(sizes, m, x, v, EPS2, eta=0.02, mode=mode) as ens:
+        s = _state(ens, len(m))
+        ek0, ep0 = ens.energy()
+        for c in sample:
+            mc, xc, vc = parts[c]
+            ra, rk, _ = oracle.force(mc, xc, vc, EPS2)
+            B, _ = bounds(mc, xc, vc, EPS2, np.arange(len(mc)), mode)
+            ga, gk = s["a"][off[c]:off[c + 1]], s["k"][off[c]:off[c + 1]]
+            assert np.all(np.linalg.norm(ga - ra, axis=1) <= B[:, 0]), c
+            assert np.all(np.linalg.norm(gk - rk, axis=1) <= B[:, 1]), c
+            rek, rep = oracle.energy(mc, xc, vc, EPS2)
+            assert abs(ek0[c] - rek) <= 1e-13 * abs(rek) and abs(ep0[c] - rep) <= 1e-13 * abs(rep)
+        ens.tune(T_END, steps=3)
+        ens.run(T_END)
+        end = _state(ens, len(m))
+        ek, ep = ens.energy()
+    assert np.all(end["t_tick"] == int(T_END * 2 ** 26))
+    de = np.abs((ek + ep - ek0 - ep0) / (ek0 + ep0))
+    print(f"\nC4 {mode}: |dE/E| at t = 1/64 median {np.median(de):.2e} max {de.max():.2e}")
+    assert de.max() < 1e-6
