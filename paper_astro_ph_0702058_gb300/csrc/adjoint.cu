@@ -108,24 +108,21 @@ __global__ void __launch_bounds__(kVjpThreads)
     }
 }
 
+// One thread per (particle, component): adds the component's ranges in order.
 __global__ void vjp_reduce_kernel(const double *__restrict__ part, int ranges, int n, DiffGrads G)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    double t[7];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) t[c] = 0.0;
-    for (int y = 0; y < ranges; ++y) {
-        const double *b = part + static_cast<size_t>(y) * 7 * n + p;
-#pragma unroll
-        for (int c = 0; c < 7; ++c) t[c] += b[static_cast<size_t>(c) * n];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        G.gxp[c][p] += t[c];
-        G.gvp[c][p] += t[3 + c];
-    }
-    G.gm[p] += t[6];
+    const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (idx >= 7LL * n) return;
+    const int c = static_cast<int>(idx / n);
+    const int p = static_cast<int>(idx - static_cast<int64_t>(c) * n);
+    double t = 0.0;
+    for (int y = 0; y < ranges; ++y) t += part[(static_cast<size_t>(y) * 7 + c) * n + p];
+    if (c < 3)
+        G.gxp[c][p] += t;
+    else if (c < 6)
+        G.gvp[c - 3][p] += t;
+    else
+        G.gm[p] += t;
 }
 
 // Transposed corrector: from the gradients of the corrected state (gx, gv, ga,
@@ -283,7 +280,7 @@ cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, fl
                                                   static_cast<int>(J.n_pad), eps2, tpr, scratch, G);
     ++*launches;
     if (r > 1) {
-        vjp_reduce_kernel<<<blocks_of(n, 256), 256, 0, s>>>(scratch, r, static_cast<int>(n), G);
+        vjp_reduce_kernel<<<blocks_of(7 * n, 256), 256, 0, s>>>(scratch, r, static_cast<int>(n), G);
         ++*launches;
     }
     return cudaGetLastError();
@@ -291,14 +288,16 @@ cudaError_t force_vjp_launch(const JStream &J, const DiffGrads &G, int64_t n, fl
 
 cudaError_t adj_correct_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches)
 {
-    adj_correct_kernel<<<blocks_of(n, 256), 256, 0, s>>>(G, static_cast<int>(n), dt);
+    const int t = n >= 152 * 256 ? 256 : 32;  // FP64-heavy rows: spread small n over more SMs
+    adj_correct_kernel<<<blocks_of(n, t), t, 0, s>>>(G, static_cast<int>(n), dt);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t adj_predict_launch(const DiffGrads &G, int64_t n, double dt, cudaStream_t s, int64_t *launches)
 {
-    adj_predict_kernel<<<blocks_of(n, 256), 256, 0, s>>>(G, static_cast<int>(n), dt);
+    const int t = n >= 152 * 256 ? 256 : 32;
+    adj_predict_kernel<<<blocks_of(n, t), t, 0, s>>>(G, static_cast<int>(n), dt);
     ++*launches;
     return cudaGetLastError();
 }

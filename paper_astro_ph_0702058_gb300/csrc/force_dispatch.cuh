@@ -77,7 +77,8 @@ cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, 
     if (split >= 32 && n_act <= 8192)
         reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
     else
-        reduce_partials_kernel<MODE><<<(n_act + nt - 1) / nt, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+        reduce_partials_kernel<MODE><<<static_cast<unsigned>((7LL * n_act + nt - 1) / nt), nt, 0, s>>>(
+            part, split, n_act, acc, jerk, pot);
     return cudaGetLastError();
 }
 

@@ -340,33 +340,30 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
     }
 }
 
-// Adds the j-range partial sums of each row in ascending range order (FP64).
+// Adds the j-range partial sums of each row in ascending range order (FP64),
+// one thread per (row, component): 7 n_act threads, reads coalesced over rows.
 template <int MODE>
 __global__ void reduce_partials_kernel(const float *__restrict__ part, int split, int n_act,
                                        double *__restrict__ acc, double *__restrict__ jerk,
                                        double *__restrict__ pot)
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_act) return;
-    double r[7];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-        double s = 0.0;
-        for (int sp = 0; sp < split; ++sp) {
-            const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
-            s += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
-            if (is_ds(MODE)) s += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
-        }
-        r[c] = s;
+    const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (idx >= 7LL * n_act) return;
+    const int c = static_cast<int>(idx / n_act);
+    const int q = static_cast<int>(idx - static_cast<int64_t>(c) * n_act);
+    double s = 0.0;
+    for (int sp = 0; sp < split; ++sp) {
+        const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
+        s += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
+        if (is_ds(MODE)) s += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
     }
-    acc[3 * static_cast<size_t>(q) + 0] = r[0];
-    acc[3 * static_cast<size_t>(q) + 1] = r[1];
-    acc[3 * static_cast<size_t>(q) + 2] = r[2];
-    jerk[3 * static_cast<size_t>(q) + 0] = r[3];
-    jerk[3 * static_cast<size_t>(q) + 1] = r[4];
-    jerk[3 * static_cast<size_t>(q) + 2] = r[5];
-    pot[q] = r[6];
+    if (c < 3)
+        acc[3 * static_cast<size_t>(q) + c] = s;
+    else if (c < 6)
+        jerk[3 * static_cast<size_t>(q) + c - 3] = s;
+    else
+        pot[q] = s;
 }
 
 // Same sums for few rows and many j-ranges: one warp per row, lane l adds the

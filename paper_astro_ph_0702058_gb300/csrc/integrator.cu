@@ -343,7 +343,9 @@ cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act,
                            cudaStream_t s, int64_t *launches)
 {
     if (n_act <= 0) return cudaSuccess;
-    correct_kernel<<<blocks_for(n_act, 128), 128, 0, s>>>(S, active, n_act, acc, jerk, t_new, ldexp(1.0, -lmax),
+    // FP64-heavy rows: small blocks spread over more SMs (GB300's FP64 rate per SM is low)
+    const int tpb = n_act >= 152 * 128 ? 128 : 32;
+    correct_kernel<<<blocks_for(n_act, tpb), tpb, 0, s>>>(S, active, n_act, acc, jerk, t_new, ldexp(1.0, -lmax),
                                                           eta, lmin, lmax, st);
     ++*launches;
     return cudaGetLastError();
