@@ -52,3 +52,32 @@ def test_reverse_mode_matches_central_differences(n, steps):
             fd.reshape(-1)[idx] = (_c_loss(*args_p, steps)[0] - _c_loss(*args_q, steps)[0]) / (2 * h)
         err = np.abs(fd - g).max() / np.abs(g).max()
         assert err < 1e-6, (name, err)
+
+
+def test_force_vjp_matches_central_differences_of_the_c_force():
+    """One force evaluation: the vector-Jacobian product against central differences of
+    S = sum_i (ga_i . a_i + gk_i . k_i) computed with the C oracle's force."""
+    n = 6
+    m, x, v = plummer_sphere(n, 41)
+    rng = np.random.default_rng(41)
+    m = m * rng.uniform(0.5, 1.5, n)
+    ga, gk = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+
+    def S(mm, xx, vv):
+        a, k, _ = oracle.force(mm, xx, vv, EPS2)
+        return float((ga * a).sum() + (gk * k).sum())
+
+    gx, gv, gm = adjoint.force_vjp(m, x, v, EPS2, ga, gk)
+    h = 1e-6
+    for name, arr, g in (("x", x, gx), ("v", v, gv), ("m", m, gm)):
+        fd = np.zeros(arr.size)
+        for idx in range(arr.size):
+            p = arr.reshape(-1).copy(); p[idx] += h  # noqa: E702
+            q = arr.reshape(-1).copy(); q[idx] -= h  # noqa: E702
+            args_p = {"m": m, "x": x, "v": v}
+            args_q = dict(args_p)
+            args_p[name] = p.reshape(arr.shape)
+            args_q[name] = q.reshape(arr.shape)
+            fd[idx] = (S(args_p["m"], args_p["x"], args_p["v"]) - S(args_q["m"], args_q["x"], args_q["v"])) / (2 * h)
+        err = np.abs(fd - g.reshape(-1)).max() / np.abs(g).max()
+        assert err < 1e-7, (name, err)

@@ -34,7 +34,20 @@ MUTANTS = {
     "schedule_tie": ("if (tn == tmin) active[na++]", "if (tn <= tmin + 1) active[na++]"),
     "energy_half": ("ep += 0.5 * m[i] * phi[i];", "ep += m[i] * phi[i];"),
     "self_term": ("if (j == i) continue;\n            double dx[3]", "double dx[3]"),
+    # the summation-check and sorted-summation oracles
+    "rsqrt_cmp_flip": ("return P < one ? -1 : (P > one ? 1 : 0);", "return P < one ? 1 : (P > one ? -1 : 0);"),
+    "rsqrt_exp_off": ("const int K = 2 * (e0 - 1) + er;", "const int K = 2 * e0 + er;"),
+    "terms_jerk_sign": ("mr3 * fmaf(-w, dx[c], dv[c])", "mr3 * fmaf(w, dx[c], dv[c])"),
+    "terms_lo_dropped": ("dx[c] = (hj - hi_i[c]) + (lj - lo_i[c]);", "dx[c] = (hj - hi_i[c]);"),
+    "terms_xv_order": ("const float xv = fmaf(dx[2], dv[2], fmaf(dx[1], dv[1], dx[0] * dv[0]));",
+                       "const float xv = dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2];"),
+    "sorted_by_value": ("const uint32_t ma = a & 0x7fffffffu, mb = b & 0x7fffffffu;", "const uint32_t ma = a, mb = b;"),
+    "sorted_largest_first": ("if (ma != mb) return ma < mb ? -1 : 1;", "if (ma != mb) return ma < mb ? 1 : -1;"),
 }
+
+# pin suite that must catch each mutant (default: the FP64 oracle's pins)
+PINS = {name: "test_oracle_sumcheck.py" for name in MUTANTS
+        if name.startswith(("rsqrt_", "terms_", "sorted_"))}
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -51,6 +64,36 @@ def test_pins_catch_mutant(tmp_path, name):
                     str(d / "oracle.c"), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, NBODY_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", PINS.get(name, "test_oracle_pins.py"))],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+ADJ_SRC = os.path.join(ROOT, "oracle", "adjoint.py")
+ADJ_MUTANTS = {
+    "vjp_r5_sign": ("gd = mj * (R3[..., None] * ga[:, None, :] - 3.0", "gd = mj * (R3[..., None] * ga[:, None, :] + 3.0"),
+    "vjp_drop_r7": ("+ 15.0 * (R7 * de * dgk)", "+ 0.0 * (R7 * de * dgk)"),
+    "vjp_roles_swapped": ("gx = gd.sum(0) - gd.sum(1)", "gx = gd.sum(1) - gd.sum(0)"),
+    "vjp_mass_drop_egk": ("gm = (R3 * dga + R3 * egk", "gm = (R3 * dga + 0.0 * egk"),
+    "loss_grad_no_pot": ("gx = 2.0 * x - m[:, None]", "gx = 2.0 * x - 0.0 * m[:, None]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ADJ_MUTANTS))
+def test_adjoint_pins_catch_mutant(tmp_path, name):
+    """The same for the numpy reverse-mode oracle: the mutated module replaces oracle.adjoint in a
+    subprocess that runs its pins."""
+    old, new = ADJ_MUTANTS[name]
+    src = open(ADJ_SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor missing: {old!r}"
+    mod = tmp_path / "adjoint_mutant.py"
+    mod.write_text(src.replace(old, new, 1))
+    boot = ("import sys, importlib.util; sys.path.insert(0, %r); import oracle; "
+            "spec = importlib.util.spec_from_file_location('oracle.adjoint', %r); "
+            "m = importlib.util.module_from_spec(spec); spec.loader.exec_module(m); "
+            "sys.modules['oracle.adjoint'] = m; oracle.adjoint = m; import pytest; "
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
+            % (ROOT, str(mod), os.path.join(ROOT, "tests", "test_oracle_adjoint.py")))
+    r = subprocess.run([sys.executable, "-c", boot], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode not in (0, 4, 5), r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
