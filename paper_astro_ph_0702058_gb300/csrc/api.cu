@@ -264,8 +264,9 @@ int check_params(const nbody_params *p)
     if (p->mode != NBODY_MODE_PLAIN && p->mode != NBODY_MODE_COMP && p->mode != NBODY_MODE_SUMCHECK &&
         p->mode != NBODY_MODE_SORTED && p->mode != NBODY_MODE_DS)
         return fail(NBODY_EINVAL, "unknown mode %d", p->mode);
-    if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256)
-        return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128 or 256");
+    if (p->j_tile != 0 && p->j_tile != 64 && p->j_tile != 128 && p->j_tile != 256 && p->j_tile != 512)
+        return fail(NBODY_EINVAL, "j_tile must be 0, 64, 128, 256 or 512");
+    if (p->j_tile == 512 && p->i_block > 1) return fail(NBODY_EINVAL, "512 threads take i_block 0 or 1");
     if (p->i_block != 0 && p->i_block != 1 && p->i_block != 2 && p->i_block != 4)
         return fail(NBODY_EINVAL, "i_block must be 0, 1, 2 or 4");
     if (p->j_split < 0) return fail(NBODY_EINVAL, "j_split must be >= 0");

@@ -25,6 +25,7 @@ namespace {
 
 int shape_index(int threads, int ipt)
 {
+    if (threads == 512) return ipt == 1 ? 9 : -1;  // one i per thread only
     const int ti = threads == 64 ? 0 : threads == 128 ? 1 : threads == 256 ? 2 : -1;
     const int ii = ipt == 1 ? 0 : ipt == 2 ? 1 : ipt == 4 ? 2 : -1;
     return (ti < 0 || ii < 0) ? -1 : ti * 3 + ii;
@@ -34,8 +35,8 @@ int shape_index(int threads, int ipt)
 // every device this library runs on is the same sm_103 part).
 int occupancy(int mode, int threads, int ipt)
 {
-    static int cache[5][9];
-    static bool filled[5][9];
+    static int cache[5][10];
+    static bool filled[5][10];
     const int si = shape_index(threads, ipt);
     if (si < 0 || mode < 0 || mode > 4) return 0;
     if (!filled[mode][si]) {

@@ -46,6 +46,7 @@ cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStr
     NB_CASE(256, 1)
     NB_CASE(256, 2)
     NB_CASE(256, 4)
+    NB_CASE(512, 1)
 #undef NB_CASE
     return cudaErrorInvalidConfiguration;
 }
@@ -65,6 +66,7 @@ int force_occupancy(int threads, int ipt)
     NB_CASE(256, 1)
     NB_CASE(256, 2)
     NB_CASE(256, 4)
+    NB_CASE(512, 1)
 #undef NB_CASE
     return 0;
 }
