@@ -98,7 +98,7 @@ typedef struct {
                          NBODY_EDTMIN (the step is still taken); zero: it is only counted */
     int i_block;      /* force tuning, 0 = automatic (1): i-particles per thread (1, 2, 4)  */
     int j_tile;       /* force tuning, 0 = automatic (256 for blocks of >= 8192 rows, else
-                         64): threads per block (64, 128 or 256)                           */
+                         64): threads per block (64, 128, 256, or 512 with i_block 1)     */
     int j_split;      /* force tuning, 0 = automatic (about 12 waves of blocks): number of
                          j-ranges (>= 1); the double-single mode always takes 128 x 1     */
     void *stream;     /* cudaStream_t for all work of the context, or NULL                  */

@@ -106,15 +106,15 @@ def test_force_every_launch_shape(torch, mode):
     m, x, v = plummer_sphere(n, 8)
     act = active_subset(n, 1111, 2)
     ref = oracle.force(m, x, v, EPS2, act)
-    for threads in (64, 128, 256):
-        for ipt in (1, 2, 4):
-            for split in (1, 3):
-                with _sim(m, x, v, EPS2, mode, j_tile=threads, i_block=ipt, j_split=split) as sim:
-                    sim.predict(0.0)
-                    got = gpu_force(sim, act)
-                    st = sim.stats()
-                assert (st["last_threads"], st["last_i_per_thread"], st["last_j_split"]) == (threads, ipt, split)
-                check_force(mode, m, x, v, EPS2, act, got, ref, f"shape {threads}x{ipt} split {split}")
+    shapes = [(t, i) for t in (64, 128, 256) for i in (1, 2, 4)] + [(512, 1)]
+    for threads, ipt in shapes:
+        for split in (1, 3):
+            with _sim(m, x, v, EPS2, mode, j_tile=threads, i_block=ipt, j_split=split) as sim:
+                sim.predict(0.0)
+                got = gpu_force(sim, act)
+                st = sim.stats()
+            assert (st["last_threads"], st["last_i_per_thread"], st["last_j_split"]) == (threads, ipt, split)
+            check_force(mode, m, x, v, EPS2, act, got, ref, f"shape {threads}x{ipt} split {split}")
 
 
 @pytest.mark.parametrize("mode", ["plain", "comp"])
