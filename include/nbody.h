@@ -284,7 +284,7 @@ typedef struct nbody_ens nbody_ens; /* opaque; owns all of its device memory */
 int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, const double *m,
                    const double *x, const double *v, double eps2, const nbody_params *p);
 
-/* Force launch shape: threads per block (64 or 128), i-particles per thread
+/* Force launch shape: threads per block (32, 64 or 128), i-particles per thread
  * (1 or 2), and j-tiles of 256 particles per work item (>= 1; each cluster is
  * cut into at most 8 j-ranges).  Errors: EINVAL for unsupported shapes. */
 int nbody_ens_set_shape(nbody_ens *e, int threads, int i_block, int tiles_per_range);

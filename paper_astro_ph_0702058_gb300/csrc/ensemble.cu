@@ -563,14 +563,16 @@ int ens_force_occupancy()
 struct EnsShape {
     int threads, ipt;
 };
-constexpr EnsShape kEnsShapes[] = {{64, 1}, {64, 2}, {128, 1}, {128, 2}};
+constexpr EnsShape kEnsShapes[] = {{32, 1}, {64, 1}, {64, 2}, {128, 1}, {128, 2}};
 
 void ens_prefetch_occupancy()
 {
+    ens_force_occupancy<kModePlain, 32, 1>();
     ens_force_occupancy<kModePlain, 64, 1>();
     ens_force_occupancy<kModePlain, 64, 2>();
     ens_force_occupancy<kModePlain, 128, 1>();
     ens_force_occupancy<kModePlain, 128, 2>();
+    ens_force_occupancy<kModeComp, 32, 1>();
     ens_force_occupancy<kModeComp, 64, 1>();
     ens_force_occupancy<kModeComp, 64, 2>();
     ens_force_occupancy<kModeComp, 128, 1>();
@@ -587,10 +589,12 @@ cudaError_t ens_force_launch(int mode, int threads, int ipt, const EnsDev &E, fl
         ++*launches;                                                        \
         return cudaGetLastError();                                          \
     }
+    NB_ENS(kModePlain, 32, 1)
     NB_ENS(kModePlain, 64, 1)
     NB_ENS(kModePlain, 64, 2)
     NB_ENS(kModePlain, 128, 1)
     NB_ENS(kModePlain, 128, 2)
+    NB_ENS(kModeComp, 32, 1)
     NB_ENS(kModeComp, 64, 1)
     NB_ENS(kModeComp, 64, 2)
     NB_ENS(kModeComp, 128, 1)
