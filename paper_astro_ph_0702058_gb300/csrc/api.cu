@@ -86,7 +86,7 @@ struct nbody_ctx {
     double *state = nullptr;  // 13 n doubles: m, x[3], v[3], a[3], k[3]
     int64_t *t = nullptr;
     int8_t *level = nullptr;
-    float4 *jbuf = nullptr;   // 4 n_pad float4: posm, vel, poslo, vello
+    float4 *jbuf = nullptr;   // 4 n_pad float4 (posm, vel, poslo, vello), then kSoaArrays n_pad floats (SoA)
     int32_t *act_force = nullptr, *act_corr = nullptr, *act_sched = nullptr;
     double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
     double *stage = nullptr;  // 6 n doubles: external forces / AoS staging
@@ -330,8 +330,8 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->state), 13 * nd * sizeof(double)), "state allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->t), nd * sizeof(int64_t)), "time allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->level), nd), "level allocation");
-    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->jbuf), 4 * static_cast<size_t>(c->n_pad) * sizeof(float4)),
-            "j-stream allocation");
+    const size_t jbytes = static_cast<size_t>(c->n_pad) * (4 * sizeof(float4) + kSoaArrays * sizeof(float));
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->jbuf), jbytes), "j-stream allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_force), nd * sizeof(int32_t)), "list allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_corr), nd * sizeof(int32_t)), "list allocation");
     NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->act_sched), nd * sizeof(int32_t)), "list allocation");
@@ -367,11 +367,12 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     c->J.vel = c->jbuf + c->n_pad;
     c->J.poslo = c->jbuf + 2 * c->n_pad;
     c->J.vello = c->jbuf + 3 * c->n_pad;
+    c->J.soa = reinterpret_cast<float *>(c->jbuf + 4 * c->n_pad);
     c->J.n_pad = c->n_pad;
 
     cudaStream_t s = c->s;
     int64_t *L = &c->stats.kernel_launches;
-    NB_INIT(cudaMemsetAsync(c->jbuf, 0, 4 * static_cast<size_t>(c->n_pad) * sizeof(float4), s), "memset");
+    NB_INIT(cudaMemsetAsync(c->jbuf, 0, jbytes, s), "memset");
     NB_INIT(pad_jstream_launch(c->J, n, s, &c->stats.kernel_launches), "padding kernel");
     NB_INIT(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s), "memset");
     NB_INIT(cudaMemsetAsync(c->state + 7 * nd, 0, 6 * nd * sizeof(double), s), "memset");

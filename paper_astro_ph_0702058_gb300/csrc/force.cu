@@ -147,6 +147,7 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     P.posm = js.posm;
     P.vel = js.vel;
     P.poslo = js.poslo;
+    P.soa = js.soa;
     P.active = active;
     P.n_act = static_cast<int>(n_act);
     P.n = static_cast<int>(n);

@@ -9,14 +9,32 @@
 
 namespace nb {
 
+// The packed kernel reads the SoA j-stream when the caller has one (library
+// contexts); a float4-only stream (no-alloc callers) goes through the packed
+// kernel's transposing variant for the automatic shapes and the scalar kernel
+// otherwise.
+template <int NT, int IPT>
+constexpr bool aos_packed_shape()
+{
+    return IPT == 1 && (NT == 64 || NT == 256);
+}
+
 template <int MODE, int NT, int IPT>
 cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
 {
     dim3 grid(cfg.n_iblk, cfg.split);
-    if constexpr (NB_PACKED && MODE != kModeCheck)
-        force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
-    else
-        force_kernel<MODE, NT, IPT, FoldLen<MODE>::value><<<grid, NT, 0, s>>>(P);
+    constexpr int PF = FoldLen<MODE>::value;
+    if constexpr (NB_PACKED && MODE != kModeCheck) {
+        if (P.soa) {
+            force_kernel_x2<MODE, NT, IPT, PF, true><<<grid, NT, 0, s>>>(P);
+            return cudaGetLastError();
+        }
+        if constexpr (aos_packed_shape<NT, IPT>()) {
+            force_kernel_x2<MODE, NT, IPT, PF, false><<<grid, NT, 0, s>>>(P);
+            return cudaGetLastError();
+        }
+    }
+    force_kernel<MODE, NT, IPT, PF><<<grid, NT, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -25,7 +43,7 @@ int occupancy_instance(int *blocks)
 {
     if constexpr (NB_PACKED && MODE != kModeCheck)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            blocks, force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value>, NT, 0);
+            blocks, force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value, true>, NT, 0);
     else
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, force_kernel<MODE, NT, IPT, FoldLen<MODE>::value>,
                                                          NT, 0);

@@ -44,6 +44,7 @@ struct ForceParams {
     const float4 *__restrict__ posm;
     const float4 *__restrict__ vel;
     const float4 *__restrict__ poslo;
+    const float *__restrict__ soa;  // SoA j-stream (kSoaArrays x n_tiles * kJTile), or NULL
     const int32_t *__restrict__ active;
     int n_act;
     int n;

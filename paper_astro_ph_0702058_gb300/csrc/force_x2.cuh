@@ -187,14 +187,19 @@ NB_UNROLL(NB_X2_UNROLL)
 #define NB_X2_BOUNDS(NT) __launch_bounds__(NT)
 #endif
 
-template <int MODE, int NT, int IPT, int PF>
+template <int MODE, int NT, int IPT, int PF, bool SOAIN>
 __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 {
+    // SOAIN: the tiles come straight from the SoA j-stream into the SoA tile
+    // buffers (one bulk copy per array, one barrier per tile); otherwise the
+    // float4 stream is staged and transposed (two barriers per tile).
     constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
+    constexpr int NA = SoaTile<MODE>::NA;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
+    constexpr uint32_t kArrBytes = kJTile * sizeof(float);
     static_assert(kJTile % PF == 0 && PF % 4 == 0, "fold length");
-    __shared__ __align__(128) float4 sj[2][NARR][kJTile];
-    __shared__ __align__(16) SoaTile<MODE> soa;
+    __shared__ __align__(128) float4 sj[SOAIN ? 1 : 2][SOAIN ? 1 : NARR][SOAIN ? 1 : kJTile];
+    __shared__ __align__(128) SoaTile<MODE> soa[SOAIN ? 2 : 1];
     __shared__ __align__(8) uint64_t bar[2];
 
     const int tid = threadIdx.x;
@@ -202,6 +207,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
     const f2_t E2 = f2_pack(P.eps2, P.eps2);
     const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
+    const size_t n_pad = static_cast<size_t>(P.n_tiles) * kJTile;
 
     I2 I[IPT];
     int gi[IPT];
@@ -249,11 +255,17 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     }
     __syncthreads();
     auto issue = [&](int tile, int b) {
-        mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
         const size_t off = static_cast<size_t>(tile) * kJTile;
-        bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
-        bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
-        if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+        if constexpr (SOAIN) {
+            mbar_arrive_expect_tx(&bar[b], NA * kArrBytes);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) bulk_g2s(soa[b].a[a], P.soa + a * n_pad + off, kArrBytes, &bar[b]);
+        } else {
+            mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
+            bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
+            bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
+            if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+        }
     };
 
     bool ok = true;
@@ -264,38 +276,51 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         const int b = it & 1;
         if (tid == 0 && t + 1 < t_end) issue(t + 1, b ^ 1);
         ok = mbar_wait_bounded(&bar[b], (it >> 1) & 1);
-        if (ok) {
-            for (int e = tid; e < kJTile; e += NT) {
-                const float4 pv = sj[b][0][e], vv = sj[b][1][e];
-                soa.a[0][e] = pv.x;
-                soa.a[1][e] = pv.y;
-                soa.a[2][e] = pv.z;
-                soa.a[3][e] = pv.w;
-                soa.a[4][e] = vv.x;
-                soa.a[5][e] = vv.y;
-                soa.a[6][e] = vv.z;
-                if (MODE == kModeComp) {
-                    const float4 lv = sj[b][NARR - 1][e];
-                    soa.a[7][e] = lv.x;
-                    soa.a[8][e] = lv.y;
-                    soa.a[9][e] = lv.z;
+        if constexpr (!SOAIN) {
+            if (ok) {
+                for (int e = tid; e < kJTile; e += NT) {
+                    const float4 pv = sj[b][0][e], vv = sj[b][1][e];
+                    soa[0].a[0][e] = pv.x;
+                    soa[0].a[1][e] = pv.y;
+                    soa[0].a[2][e] = pv.z;
+                    soa[0].a[3][e] = pv.w;
+                    soa[0].a[4][e] = vv.x;
+                    soa[0].a[5][e] = vv.y;
+                    soa[0].a[6][e] = vv.z;
+                    if (MODE == kModeComp) {
+                        const float4 lv = sj[b][NARR - 1][e];
+                        soa[0].a[7][e] = lv.x;
+                        soa[0].a[8][e] = lv.y;
+                        soa[0].a[9][e] = lv.z;
+                    }
                 }
             }
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                it_stop = it;
+                break;
+            }
         }
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            it_stop = it;
-            break;
-        }
+        // (with SOAIN a thread whose wait gave up computes on a partial tile; the
+        // barrier below stops every thread before any result is written)
+        const SoaTile<MODE> &T = soa[SOAIN ? b : 0];
         const int j0 = t * kJTile;
         bool self_tile = false;
 #pragma unroll
         for (int u = 0; u < IPT; ++u) self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
         if (self_tile)
-            tile_sums_x2<MODE, IPT, PF, true>(soa, j0, I, gi, E2, NEG3, tot, lo);
+            tile_sums_x2<MODE, IPT, PF, true>(T, j0, I, gi, E2, NEG3, tot, lo);
         else
-            tile_sums_x2<MODE, IPT, PF, false>(soa, j0, I, gi, E2, NEG3, tot, lo);
-        __syncthreads();
+            tile_sums_x2<MODE, IPT, PF, false>(T, j0, I, gi, E2, NEG3, tot, lo);
+        if constexpr (SOAIN) {
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                it_stop = it;
+                break;
+            }
+        } else {
+            __syncthreads();
+        }
     }
 
     if (!ok) {

@@ -45,6 +45,22 @@ __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, do
             J.vello[i] = make_float4(__double2float_rn(vp[0] - static_cast<double>(hvx)),
                                      __double2float_rn(vp[1] - static_cast<double>(hvy)),
                                      __double2float_rn(vp[2] - static_cast<double>(hvz)), 0.f);
+        if (J.soa) {
+            float *a = J.soa + i;
+            const int64_t np = J.n_pad;
+            a[0] = hx;
+            a[np] = hy;
+            a[2 * np] = hz;
+            a[3 * np] = hm;
+            a[4 * np] = hvx;
+            a[5 * np] = hvy;
+            a[6 * np] = hvz;
+            if (lo_parts) {
+                a[7 * np] = __double2float_rn(xp[0] - static_cast<double>(hx));
+                a[8 * np] = __double2float_rn(xp[1] - static_cast<double>(hy));
+                a[9 * np] = __double2float_rn(xp[2] - static_cast<double>(hz));
+            }
+        }
     }
 }
 
@@ -295,13 +311,15 @@ __global__ void soa_to_aos_kernel(const double *c0, const double *c1, const doub
 
 // Padding of the j-stream: massless particles far away (r^2 ~ 3e30), so a
 // padding pair adds exactly zero even with eps = 0 and a particle at the origin.
-__global__ void pad_jstream_kernel(float4 *posm, float4 *vel, float4 *poslo, int64_t n, int64_t n_pad)
+__global__ void pad_jstream_kernel(float4 *posm, float4 *vel, float4 *poslo, float *soa, int64_t n, int64_t n_pad)
 {
     for (int64_t i = n + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_pad;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         posm[i] = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.f);
         vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         poslo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (soa)
+            for (int a = 0; a < kSoaArrays; ++a) soa[a * n_pad + i] = a < 3 ? kPadPosition : 0.f;
     }
 }
 
@@ -317,7 +335,7 @@ __global__ void iota_kernel(int32_t *a, int64_t n)
 cudaError_t pad_jstream_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches)
 {
     if (J.n_pad <= n) return cudaSuccess;
-    pad_jstream_kernel<<<1, kThreads, 0, s>>>(J.posm, J.vel, J.poslo, n, J.n_pad);
+    pad_jstream_kernel<<<1, kThreads, 0, s>>>(J.posm, J.vel, J.poslo, J.soa, n, J.n_pad);
     ++*launches;
     return cudaGetLastError();
 }

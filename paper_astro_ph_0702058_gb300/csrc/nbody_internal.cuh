@@ -66,8 +66,13 @@ struct JStream {
     float4 *vel;    // (vx, vy, vz, 0)
     float4 *poslo;  // (x - x_hi, y - y_hi, z - z_hi, m - m_hi) rounded to float; compensated (m part 0) and DS modes
     float4 *vello;  // (vx - vx_hi, vy - vy_hi, vz - vz_hi, 0) rounded to float; DS mode
+    // The same stream as structure of arrays, kSoaArrays x n_pad floats: x_hi, y_hi, z_hi, m_hi,
+    // vx_hi, vy_hi, vz_hi, x_lo, y_lo, z_lo (lo parts in the compensated modes).  The packed
+    // force kernel copies its tiles straight from here; NULL (no-alloc callers) means AoS only.
+    float *soa;
     int64_t n_pad;
 };
+constexpr int kSoaArrays = 10;
 
 struct ForceConfig {
     int threads;          // threads per block

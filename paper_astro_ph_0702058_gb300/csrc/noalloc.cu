@@ -135,6 +135,7 @@ extern "C" int nbody_force_noalloc(const float *posm, const float *vel, const fl
     js.vel = reinterpret_cast<float4 *>(const_cast<float *>(vel));
     js.poslo = reinterpret_cast<float4 *>(const_cast<float *>(mode == NBODY_MODE_COMP ? poslo : posm));
     js.vello = nullptr;
+    js.soa = nullptr;  // the caller's stream is AoS only
     js.n_pad = n_pad;
     int64_t launches = 0;
     e = force_launch(mode, js, n, active, n_act, eps2, cfg, acc, jerk, pot, A.partials,
