@@ -191,12 +191,31 @@ __global__ void ens_predict_kernel(const EnsDev E, double tick, int comp)
         for (int q = 0; q < 3; ++q) predict_dim(E.S.x[q][i], E.S.v[q][i], E.S.a[q][i], E.S.k[q][i], dt, xp[q], vp[q]);
         const int64_t j = E.joff[c] + (i - E.off[c]);
         const float hx = __double2float_rn(xp[0]), hy = __double2float_rn(xp[1]), hz = __double2float_rn(xp[2]);
-        E.J.posm[j] = make_float4(hx, hy, hz, __double2float_rn(E.S.m[i]));
-        E.J.vel[j] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
-        if (comp)
-            E.J.poslo[j] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
-                                       __double2float_rn(xp[1] - static_cast<double>(hy)),
-                                       __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+        const float hm = __double2float_rn(E.S.m[i]);
+        const float hvx = __double2float_rn(vp[0]), hvy = __double2float_rn(vp[1]), hvz = __double2float_rn(vp[2]);
+        E.J.posm[j] = make_float4(hx, hy, hz, hm);
+        E.J.vel[j] = make_float4(hvx, hvy, hvz, 0.f);
+        float lx = 0.f, ly = 0.f, lz = 0.f;
+        if (comp) {
+            lx = __double2float_rn(xp[0] - static_cast<double>(hx));
+            ly = __double2float_rn(xp[1] - static_cast<double>(hy));
+            lz = __double2float_rn(xp[2] - static_cast<double>(hz));
+            E.J.poslo[j] = make_float4(lx, ly, lz, 0.f);
+        }
+        float *a = E.J.soa + j;
+        const int64_t np = E.J.n_pad;
+        a[0] = hx;
+        a[np] = hy;
+        a[2 * np] = hz;
+        a[3 * np] = hm;
+        a[4 * np] = hvx;
+        a[5 * np] = hvy;
+        a[6 * np] = hvz;
+        if (comp) {
+            a[7 * np] = lx;
+            a[8 * np] = ly;
+            a[9 * np] = lz;
+        }
     }
 }
 
@@ -209,8 +228,11 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
     constexpr int PF = FoldLen<MODE>::value;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
     constexpr bool kPacked = NB_PACKED != 0;
-    __shared__ __align__(128) float4 sj[2][NARR][kJTile];
-    __shared__ __align__(16) typename std::conditional<kPacked, SoaTile<MODE>, char>::type soa;
+    constexpr int NA = SoaTile<MODE>::NA;
+    constexpr uint32_t kArrBytes = kJTile * sizeof(float);
+    // packed: tiles copied from the SoA j-stream into two SoA buffers; scalar: float4 staging
+    __shared__ __align__(128) float4 sj[kPacked ? 1 : 2][kPacked ? 1 : NARR][kPacked ? 1 : kJTile];
+    __shared__ __align__(128) typename std::conditional<kPacked, SoaTile<MODE>, char>::type soa[2];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long s_w;
     const int tid = threadIdx.x;
@@ -223,11 +245,18 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
     }
     __syncthreads();
     auto issue = [&](int64_t tile, int b) {
-        mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
         const size_t off = static_cast<size_t>(tile) * kJTile;
-        bulk_g2s(sj[b][0], E.J.posm + off, kTileBytes, &bar[b]);
-        bulk_g2s(sj[b][1], E.J.vel + off, kTileBytes, &bar[b]);
-        if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], E.J.poslo + off, kTileBytes, &bar[b]);
+        if constexpr (kPacked) {
+            mbar_arrive_expect_tx(&bar[b], NA * kArrBytes);
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                bulk_g2s(soa[b].a[a], E.J.soa + a * static_cast<size_t>(E.J.n_pad) + off, kArrBytes, &bar[b]);
+        } else {
+            mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
+            bulk_g2s(sj[b][0], E.J.posm + off, kTileBytes, &bar[b]);
+            bulk_g2s(sj[b][1], E.J.vel + off, kTileBytes, &bar[b]);
+            if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], E.J.poslo + off, kTileBytes, &bar[b]);
+        }
     };
     const long long W = E.item_pfx[E.n_cl];
     unsigned int g = 0;  // tiles this block has consumed: buffer g & 1, phase (g >> 1) & 1
@@ -305,25 +334,18 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
             if (tid == 0 && t + 1 < t_end) issue(jt0 + t + 1, b ^ 1);
             ok = mbar_wait_bounded(&bar[b], (g >> 1) & 1);
             if constexpr (kPacked) {
-                // same order as the single-system packed kernel: transpose, then the packed loop
-                if (ok) {
-                    for (int e = tid; e < kJTile; e += NT) {
-                        const float4 pv = sj[b][0][e], vv = sj[b][1][e];
-                        soa.a[0][e] = pv.x;
-                        soa.a[1][e] = pv.y;
-                        soa.a[2][e] = pv.z;
-                        soa.a[3][e] = pv.w;
-                        soa.a[4][e] = vv.x;
-                        soa.a[5][e] = vv.y;
-                        soa.a[6][e] = vv.z;
-                        if (MODE == kModeComp) {
-                            const float4 lv = sj[b][NARR - 1][e];
-                            soa.a[7][e] = lv.x;
-                            soa.a[8][e] = lv.y;
-                            soa.a[9][e] = lv.z;
-                        }
-                    }
-                }
+                // the single-system packed kernel's tile loop: SoA tile, packed pairs, one barrier
+                // (a thread whose wait gave up computes on a partial tile; the barrier stops all
+                // threads before anything is written)
+                const int j0 = static_cast<int>(jo) + t * kJTile;
+                bool self_tile = false;
+#pragma unroll
+                for (int u = 0; u < IPT; ++u)
+                    self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
+                if (self_tile)
+                    tile_sums_x2<MODE, IPT, PF, true>(soa[b], j0, I, gi, E2, NEG3, tot, lo_);
+                else
+                    tile_sums_x2<MODE, IPT, PF, false>(soa[b], j0, I, gi, E2, NEG3, tot, lo_);
                 if (__syncthreads_or(!ok)) {
                     if (tid == 0) {
                         mbar_wait_bounded(&bar[b], (g >> 1) & 1);
@@ -332,16 +354,6 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
                     }
                     return;
                 }
-                const int j0 = static_cast<int>(jo) + t * kJTile;
-                bool self_tile = false;
-#pragma unroll
-                for (int u = 0; u < IPT; ++u)
-                    self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
-                if (self_tile)
-                    tile_sums_x2<MODE, IPT, PF, true>(soa, j0, I, gi, E2, NEG3, tot, lo_);
-                else
-                    tile_sums_x2<MODE, IPT, PF, false>(soa, j0, I, gi, E2, NEG3, tot, lo_);
-                __syncthreads();
                 continue;
             }
             if (ok) {
@@ -530,6 +542,7 @@ __global__ void ens_pad_kernel(const EnsDev E)
             E.J.posm[j] = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.f);
             E.J.vel[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             E.J.poslo[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int a = 0; a < kSoaArrays; ++a) E.J.soa[a * E.J.n_pad + j] = a < 3 ? kPadPosition : 0.f;
         }
     }
 }
@@ -800,7 +813,8 @@ int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, co
     NB_EI(cudaMalloc(&e->state, 13 * nd * sizeof(double)), "state allocation");
     NB_EI(cudaMalloc(&e->t, nd * sizeof(int64_t)), "time allocation");
     NB_EI(cudaMalloc(&e->level, nd), "level allocation");
-    NB_EI(cudaMalloc(&e->jbuf, 3 * static_cast<size_t>(jt) * sizeof(float4)), "j-stream allocation");
+    const size_t jbytes = static_cast<size_t>(jt) * (3 * sizeof(float4) + kSoaArrays * sizeof(float));
+    NB_EI(cudaMalloc(&e->jbuf, jbytes), "j-stream allocation");
     NB_EI(cudaMalloc(&e->off, (nc + 1) * sizeof(int64_t)), "offsets");
     NB_EI(cudaMalloc(&e->joff, nc * sizeof(int64_t)), "offsets");
     NB_EI(cudaMalloc(&e->cl_of, nd * sizeof(int32_t)), "cluster map");
@@ -847,6 +861,7 @@ int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, co
     E.J.posm = e->jbuf;
     E.J.vel = e->jbuf + jt;
     E.J.poslo = e->jbuf + 2 * jt;
+    E.J.soa = reinterpret_cast<float *>(e->jbuf + 3 * jt);
     E.J.n_pad = jt;
     E.t_blk = e->t_blk;
     E.n_act = e->n_act;
@@ -866,7 +881,7 @@ int nbody_ens_init(nbody_ens **out, int64_t n_clusters, const int64_t *sizes, co
     NB_EI(cudaMemcpyAsync(e->off, off.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
     NB_EI(cudaMemcpyAsync(e->joff, joff.data(), nc * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
     NB_EI(cudaMemcpyAsync(e->cl_of, clmap.data(), nd * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
-    NB_EI(cudaMemsetAsync(e->jbuf, 0, 3 * static_cast<size_t>(jt) * sizeof(float4), s), "memset");
+    NB_EI(cudaMemsetAsync(e->jbuf, 0, jbytes, s), "memset");
     NB_EI(cudaMemsetAsync(e->state + 7 * nd, 0, 6 * nd * sizeof(double), s), "memset");
     NB_EI(cudaMemsetAsync(e->t, 0, nd * sizeof(int64_t), s), "memset");
     NB_EI(cudaMemsetAsync(e->blocks, 0, nc * sizeof(long long), s), "memset");
