@@ -35,6 +35,11 @@
 #ifndef NB_X2_JSTEP
 #define NB_X2_JSTEP 4
 #endif
+// Tiles per barrier in the SoA-tile kernel: each group of NB_X2_TGROUP tiles
+// arrives on one mbarrier and ends with one block barrier.
+#ifndef NB_X2_TGROUP
+#define NB_X2_TGROUP 2
+#endif
 #define NB_PRAGMA(x) _Pragma(#x)
 #define NB_UNROLL(n) NB_PRAGMA(unroll n)
 
@@ -199,7 +204,9 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     constexpr uint32_t kArrBytes = kJTile * sizeof(float);
     static_assert(kJTile % PF == 0 && PF % 4 == 0, "fold length");
     __shared__ __align__(128) float4 sj[SOAIN ? 1 : 2][SOAIN ? 1 : NARR][SOAIN ? 1 : kJTile];
-    __shared__ __align__(128) SoaTile<MODE> soa[SOAIN ? 2 : 1];
+    // small blocks keep one tile per group: their occupancy is set by shared memory
+    constexpr int TG = (SOAIN && NT >= 128) ? NB_X2_TGROUP : 1;
+    __shared__ __align__(128) SoaTile<MODE> soa[SOAIN ? 2 * TG : 1];
     __shared__ __align__(8) uint64_t bar[2];
 
     const int tid = threadIdx.x;
@@ -254,12 +261,18 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         mbar_fence_init();
     }
     __syncthreads();
-    auto issue = [&](int tile, int b) {
-        const size_t off = static_cast<size_t>(tile) * kJTile;
+    // group g holds tiles t_begin + g TG .. (at most TG of them)
+    const int n_g = t_end > t_begin ? (t_end - t_begin + TG - 1) / TG : 0;
+    auto issue = [&](int gidx, int b) {
+        const int t0 = t_begin + gidx * TG;
+        const size_t off = static_cast<size_t>(t0) * kJTile;
         if constexpr (SOAIN) {
-            mbar_arrive_expect_tx(&bar[b], NA * kArrBytes);
+            const int nt = min(TG, t_end - t0);
+            mbar_arrive_expect_tx(&bar[b], nt * NA * kArrBytes);
+            for (int k = 0; k < nt; ++k)
 #pragma unroll
-            for (int a = 0; a < NA; ++a) bulk_g2s(soa[b].a[a], P.soa + a * n_pad + off, kArrBytes, &bar[b]);
+                for (int a = 0; a < NA; ++a)
+                    bulk_g2s(soa[b * TG + k].a[a], P.soa + a * n_pad + off + k * kJTile, kArrBytes, &bar[b]);
         } else {
             mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
             bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
@@ -270,11 +283,10 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 
     bool ok = true;
     int it_stop = 0;
-    if (tid == 0 && t_begin < t_end && !P.skip_first_copy) issue(t_begin, 0);
-    for (int t = t_begin; t < t_end; ++t) {
-        const int it = t - t_begin;
+    if (tid == 0 && n_g > 0 && !P.skip_first_copy) issue(0, 0);
+    for (int it = 0; it < n_g; ++it) {
         const int b = it & 1;
-        if (tid == 0 && t + 1 < t_end) issue(t + 1, b ^ 1);
+        if (tid == 0 && it + 1 < n_g) issue(it + 1, b ^ 1);
         ok = mbar_wait_bounded(&bar[b], (it >> 1) & 1);
         if constexpr (!SOAIN) {
             if (ok) {
@@ -303,15 +315,21 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         }
         // (with SOAIN a thread whose wait gave up computes on a partial tile; the
         // barrier below stops every thread before any result is written)
-        const SoaTile<MODE> &T = soa[SOAIN ? b : 0];
-        const int j0 = t * kJTile;
-        bool self_tile = false;
+        const int t0 = t_begin + it * TG;
+        const int nt = min(TG, t_end - t0);
+#pragma unroll 1
+        for (int k = 0; k < nt; ++k) {
+            const SoaTile<MODE> &T = soa[SOAIN ? b * TG + k : 0];
+            const int j0 = (t0 + k) * kJTile;
+            bool self_tile = false;
 #pragma unroll
-        for (int u = 0; u < IPT; ++u) self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
-        if (self_tile)
-            tile_sums_x2<MODE, IPT, PF, true>(T, j0, I, gi, E2, NEG3, tot, lo);
-        else
-            tile_sums_x2<MODE, IPT, PF, false>(T, j0, I, gi, E2, NEG3, tot, lo);
+            for (int u = 0; u < IPT; ++u)
+                self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
+            if (self_tile)
+                tile_sums_x2<MODE, IPT, PF, true>(T, j0, I, gi, E2, NEG3, tot, lo);
+            else
+                tile_sums_x2<MODE, IPT, PF, false>(T, j0, I, gi, E2, NEG3, tot, lo);
+        }
         if constexpr (SOAIN) {
             if (__syncthreads_or(!ok)) {
                 ok = false;
@@ -327,7 +345,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         if (tid == 0) {
             const int b = it_stop & 1;
             mbar_wait_bounded(&bar[b], (it_stop >> 1) & 1);
-            if (t_begin + it_stop + 1 < t_end) mbar_wait_bounded(&bar[b ^ 1], ((it_stop + 1) >> 1) & 1);
+            if (it_stop + 1 < n_g) mbar_wait_bounded(&bar[b ^ 1], ((it_stop + 1) >> 1) & 1);
             atomicOr(&P.st->flags, kFlagTimeout);
         }
         return;
