@@ -4,10 +4,12 @@
 // in one instruction.  The pair loop issues ~30 instructions per pair in the
 // scalar form and is limited by instruction dispatch, not by the FP32 pipe;
 // here two consecutive j share one packed instruction stream:
-//   - j-tiles arrive as float4 by bulk async copy (double-buffered, as in the
-//     scalar kernel) and are transposed once per tile into structure-of-
-//     arrays shared memory, so one 128-bit shared load yields two packed
-//     (j, j+1) pairs of a component;
+//   - j-tiles arrive in structure-of-arrays shared memory, one bulk async
+//     copy per array from the SoA j-stream, double-buffered, two tiles per
+//     mbarrier and block barrier for blocks of 128 threads or more (a
+//     float4-only stream, as no-alloc callers pass, is staged and transposed
+//     instead); one 128-bit shared load then yields two packed (j, j+1)
+//     pairs of a component;
 //   - each i-particle is broadcast once into packed registers {x_i, x_i};
 //   - the pair term of Appendix A runs on packed operands, with the MUFU
 //     reciprocal square root applied to each half;
