@@ -188,6 +188,21 @@ KERNEL_SOURCES = ("paper_astro_ph_0702058_gb300/csrc/force_impl.cuh", "paper_ast
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic_n1048576.json")
 
 
+def kernel_code_digest():
+    """SHA-256 of the force kernel's sources with // comments and blank lines removed, so that
+    only code changes invalidate a recorded measurement."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel)) as f:
+            for line in f:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
 def measured_traffic(mode, n, launch=None):
     """DRAM bytes per force launch from the committed ncu capture, or None when that
     capture was of another size or launch shape, or the kernel source has changed since."""
@@ -197,10 +212,7 @@ def measured_traffic(mode, n, launch=None):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+    h = hashlib.sha256(kernel_code_digest().encode())
     if rec.get("source_sha256") != h.hexdigest() or rec.get("n") != n or mode not in rec:
         return None
     if launch is not None and list(rec[mode].get("launch", [])) != list(launch):
