@@ -218,6 +218,7 @@ typedef struct {
     int last_i_per_thread;
     int last_j_split;
     int mode;
+    int64_t graph_blocks;  /* block steps nbody_step ran as one replayed CUDA graph */
 } nbody_stats;
 
 int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);
@@ -241,6 +242,14 @@ void nbody_debug_fail_alloc(int k);
  * returns, and the call reports NBODY_ETIMEOUT.  Nothing faults or hangs and
  * the context stays usable.  Exercises the failure path of the device waits. */
 void nbody_debug_skip_tile_copy(int on);
+
+/* Test switch (default on): nbody_step replays blocks small enough for one
+ * captured CUDA graph (predictor, force, corrector, the next block's schedule
+ * and its read-back, reading the block time and size on the device) instead
+ * of launching each kernel from the host.  The graph is used only when its
+ * launch shape is the one the separate launches would take, so both give the
+ * same results bit for bit; off (0) forces the separate launches. */
+void nbody_debug_step_graphs(int on);
 
 /* ------------------------------------------------------------ differentiation
  * Reverse mode of a shared-step rollout: the force of Eq. (Force) at t = 0,

@@ -14,7 +14,8 @@ from ._lib import (NBODY_MODE_COMP, NBODY_MODE_DS, NBODY_MODE_PLAIN, NBODY_MODE_
                    nbody_diff_rollout,
                    nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
                    nbody_ens_init, nbody_ens_run, nbody_ens_set_shape, nbody_ens_step, nbody_ens_tune,
-                   nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_default_params, nbody_energy,
+                   nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_debug_step_graphs,
+                   nbody_default_params, nbody_energy,
                    nbody_force, nbody_force_noalloc, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
                    nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
                    nbody_strerror, nbody_sync)

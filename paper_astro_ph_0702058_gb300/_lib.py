@@ -39,7 +39,7 @@ NBODY_MODE_DS = 4
 EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",
            "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state",
            "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
-           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_force_noalloc",
+           "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_debug_step_graphs", "nbody_force_noalloc",
            "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
            "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_ens_free",
            "nbody_diff_rollout")
@@ -55,7 +55,7 @@ class nbody_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_pad", C.c_int64), ("blocks", C.c_int64), ("below_dt_min", C.c_int64),
                 ("nonfinite", C.c_int64), ("force_calls", C.c_int64), ("pairs", C.c_int64),
                 ("kernel_launches", C.c_int64), ("last_threads", C.c_int), ("last_i_per_thread", C.c_int),
-                ("last_j_split", C.c_int), ("mode", C.c_int)]
+                ("last_j_split", C.c_int), ("mode", C.c_int), ("graph_blocks", C.c_int64)]
 
 
 class NBodyError(RuntimeError):
@@ -102,6 +102,8 @@ def lib():
             L.nbody_debug_fail_alloc.restype = None
             L.nbody_debug_skip_tile_copy.argtypes = [C.c_int]
             L.nbody_debug_skip_tile_copy.restype = None
+            L.nbody_debug_step_graphs.argtypes = [C.c_int]
+            L.nbody_debug_step_graphs.restype = None
             L.nbody_force_noalloc.argtypes = [P, P, P, C.c_int64, P, C.c_int64, C.c_double, C.c_int, P, P, P, P]
             L.nbody_force_noalloc.restype = C.c_int
             I = C.POINTER(C.c_int)
@@ -270,6 +272,10 @@ def nbody_debug_fail_alloc(k: int) -> None:
 
 def nbody_debug_skip_tile_copy(on: bool) -> None:
     lib().nbody_debug_skip_tile_copy(1 if on else 0)
+
+
+def nbody_debug_step_graphs(on: bool) -> None:
+    lib().nbody_debug_step_graphs(1 if on else 0)
 
 
 def nbody_force_noalloc(posm, vel, poslo, n: int, active, n_act: int, eps2: float, mode: int,

@@ -19,7 +19,8 @@ using namespace nb;
 namespace {
 
 thread_local char g_err[512] = "";
-int g_fail_alloc = 0;  // allocation-failure injection countdown (test hook)
+int g_fail_alloc = 0;    // allocation-failure injection countdown (test hook)
+int g_step_graphs = 1;   // nbody_step replays small blocks as a CUDA graph (test switch)
 
 int fail(int code, const char *fmt, ...)
 {
@@ -108,6 +109,13 @@ struct nbody_ctx {
     JStream J{};
     int64_t t_max = 0;      // largest t_i (ticks)
     int64_t t_pred = 0;     // time of the last prediction (ticks)
+    // nbody_step's small-block graph: predict, force, correct, schedule the next block and read
+    // it back, all sized for graph_rows rows and reading the block time and size on the device
+    cudaGraphExec_t step_graph = nullptr;
+    int64_t graph_rows = 0;
+    ForceConfig graph_cfg{};
+    void *graph_partials = nullptr;
+    int64_t graph_launches = 0;  // kernel nodes per replay
     bool pred_valid = false;
     int64_t force_n_act = -1;
     nbody_stats stats{};
@@ -117,6 +125,7 @@ namespace {
 
 void release(nbody_ctx *c)
 {
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     void *dev[] = {c->state, c->t, c->level, c->jbuf, c->act_force, c->act_corr, c->act_sched,
                    c->f_acc, c->f_jerk, c->f_pot, c->stage, c->partials, c->sched_scratch,
                    c->sched_out, c->st, c->phi, c->e_out, c->trange};
@@ -484,6 +493,70 @@ int nbody_correct(nbody_ctx *c, const int32_t *active, int64_t n_act, const doub
     return correct_internal(c, c->act_corr, n_act, fa, fj);
 }
 
+namespace {
+
+// Rows the small-block graph is sized for: its force grid (rows / 64 x j-ranges)
+// stays near 2048 blocks, so blocks beyond the actual size exit at little cost.
+int64_t graph_rows_for(const nbody_ctx *c)
+{
+    const int64_t n_tiles = c->n_pad / kJTile;
+    const int64_t by_grid = 64 * std::max<int64_t>(1, 2048 / n_tiles);
+    return std::min<int64_t>({c->n, by_grid, 8191});
+}
+
+bool same_shape(const ForceConfig &a, const ForceConfig &b)
+{
+    return a.threads == b.threads && a.ipt == b.ipt && a.split == b.split && a.tiles_per_split == b.tiles_per_split;
+}
+
+// Captures the graph once (and again when the partial-sum scratch moved).
+int build_step_graph(nbody_ctx *c)
+{
+    if (c->step_graph && c->graph_partials == c->partials) return NBODY_OK;
+    if (c->step_graph) {
+        cudaGraphExecDestroy(c->step_graph);
+        c->step_graph = nullptr;
+    }
+    const int64_t rows = c->graph_rows;
+    const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, c->graph_cfg, rows));
+    if (rp != NBODY_OK) return rp;
+    cudaStream_t cs = nullptr;
+    NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    int64_t launches = 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = predict_launch(c->S, c->J, 0, c->p.lmax, predict_lo_parts(c->p.mode), cs, &launches,
+                                        &c->sched_out->t_blk);
+        if (e2 == cudaSuccess)
+            e2 = force_launch(c->p.mode, c->J, c->n, c->act_sched, rows, c->eps2, c->graph_cfg, c->f_acc, c->f_jerk,
+                              c->f_pot, c->partials, c->st, cs, &launches, &c->sched_out->n_act);
+        if (e2 == cudaSuccess)
+            e2 = correct_launch(c->S, c->act_sched, rows, c->f_acc, c->f_jerk, 0, c->p.eta, c->p.lmin, c->p.lmax,
+                                c->st, cs, &launches, c->sched_out);
+        if (e2 == cudaSuccess)
+            e2 = schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, &launches);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, cs);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        c->step_graph = nullptr;
+        return cuda_fail(e, "step graph capture");
+    }
+    c->graph_partials = c->partials;
+    c->graph_launches = launches;
+    return NBODY_OK;
+}
+
+}  // namespace
+
 int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
 {
     if (!c) return fail(NBODY_EINVAL, "nbody_step: null context");
@@ -494,12 +567,47 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     if (tend % dtmax != 0) return fail(NBODY_EINVAL, "nbody_step: t_end must be a multiple of dt_max = 2^-%d", c->p.lmin);
     if (tend < c->t_max) return fail(NBODY_EINVAL, "nbody_step: t_end is before the current time");
     int64_t done = 0;
-    for (;;) {
-        if (max_steps > 0 && done >= max_steps) break;
-        int64_t tb, na;
-        r = schedule_internal(c, &tb, &na);
-        if (r != NBODY_OK) break;
-        if (tb > tend) break;
+    // Small blocks replay one graph (predict, force, correct, next schedule and its read-back) when its
+    // launch shape is the one the separate launches would take, so both give the same bits.
+    const bool packed = force_reads_device_rows(c->p.mode);
+    if (g_step_graphs && packed && c->graph_rows == 0) {
+        c->graph_rows = graph_rows_for(c);
+        if (force_choose(c->p.mode, c->graph_rows, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
+                         &c->graph_cfg) != NBODY_OK)
+            c->graph_rows = -1;
+    }
+    int64_t tb = 0, na = 0;
+    r = schedule_internal(c, &tb, &na);
+    while (r == NBODY_OK && tb <= tend && !(max_steps > 0 && done >= max_steps)) {
+        ForceConfig cfg{};
+        bool use_graph = g_step_graphs && packed && c->graph_rows > 0 && na <= c->graph_rows &&
+                         force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block,
+                                      c->p.j_split, &cfg) == NBODY_OK &&
+                         same_shape(cfg, c->graph_cfg);
+        if (use_graph) {
+            r = build_step_graph(c);
+            if (r != NBODY_OK) break;
+            NB_CUDA(cudaGraphLaunch(c->step_graph, c->s), "step graph launch");
+            NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+            c->stats.kernel_launches += c->graph_launches;
+            c->stats.force_calls += 1;
+            c->stats.pairs += na * (c->n - 1);
+            c->stats.blocks += 1;
+            c->stats.graph_blocks += 1;
+            c->stats.last_threads = cfg.threads;
+            c->stats.last_i_per_thread = cfg.ipt;
+            c->stats.last_j_split = cfg.split;
+            c->t_max = std::max(c->t_max, tb);
+            c->t_pred = tb;
+            c->pred_valid = false;
+            c->force_n_act = -1;
+            ++done;
+            r = absorb_status(c);
+            if (r != NBODY_OK) break;
+            tb = c->sched_host->t_blk;
+            na = c->sched_host->n_act;
+            continue;
+        }
         r = predict_internal(c, tb);
         if (r != NBODY_OK) break;
         NB_CUDA(cudaMemcpyAsync(c->act_force, c->act_sched, static_cast<size_t>(na) * sizeof(int32_t),
@@ -510,6 +618,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
         r = correct_internal(c, c->act_sched, na, c->f_acc, c->f_jerk);
         if (r != NBODY_OK) break;
         ++done;
+        r = schedule_internal(c, &tb, &na);
     }
     if (n_steps) *n_steps = done;
     if (r != NBODY_OK) return r;
@@ -777,5 +886,7 @@ const char *nbody_last_error(void) { return g_err; }
 void nbody_debug_fail_alloc(int k) { g_fail_alloc = k > 0 ? k : 0; }
 
 void nbody_debug_skip_tile_copy(int on) { nb::g_skip_first_copy = on ? 1 : 0; }
+
+void nbody_debug_step_graphs(int on) { g_step_graphs = on ? 1 : 0; }
 
 }  // extern "C"

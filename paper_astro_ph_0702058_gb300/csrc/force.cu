@@ -2,7 +2,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "force_impl.cuh"
+#include "force_x2.cuh"
 
 namespace nb {
 
@@ -11,15 +11,20 @@ cudaError_t force_dispatch_comp(const ForceParams &P, const ForceConfig &cfg, cu
 int force_occupancy_plain(int threads, int ipt);
 int force_occupancy_comp(int threads, int ipt);
 cudaError_t reduce_plain(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
-                         cudaStream_t s);
+                         cudaStream_t s, const long long *n_act_dev);
 cudaError_t reduce_comp(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
-                        cudaStream_t s);
+                        cudaStream_t s, const long long *n_act_dev);
 cudaError_t force_dispatch_check(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s);
 int force_occupancy_check(int threads, int ipt);
 cudaError_t reduce_check(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
-                         cudaStream_t s);
+                         cudaStream_t s, const long long *n_act_dev);
 
 int g_skip_first_copy = 0;  // test hook (nbody_debug_skip_tile_copy)
+
+bool force_reads_device_rows(int mode)
+{
+    return NB_PACKED && (mode == kModePlain || mode == kModeComp);
+}
 
 namespace {
 
@@ -122,7 +127,7 @@ size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
 
 cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active, int64_t n_act, double eps2_d,
                          const ForceConfig &cfg, double *acc, double *jerk, double *pot, void *partials,
-                         DevStatus *st, cudaStream_t s, int64_t *launches)
+                         DevStatus *st, cudaStream_t s, int64_t *launches, const long long *n_act_dev)
 {
     if (n_act <= 0) return cudaSuccess;
     const float eps2 = static_cast<float>(eps2_d);
@@ -131,7 +136,8 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
         if (e != cudaSuccess) return e;
         ++*launches;
         if (cfg.split > 1) {
-            e = reduce_comp(static_cast<float *>(partials), cfg.split, static_cast<int>(n_act), acc, jerk, pot, s);
+            e = reduce_comp(static_cast<float *>(partials), cfg.split, static_cast<int>(n_act), acc, jerk, pot, s,
+                            nullptr);
             if (e != cudaSuccess) return e;
             ++*launches;
         }
@@ -150,6 +156,7 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     P.soa = js.soa;
     P.active = active;
     P.n_act = static_cast<int>(n_act);
+    P.n_act_dev = n_act_dev;
     P.n = static_cast<int>(n);
     P.n_tiles = static_cast<int>(js.n_pad / kJTile);
     P.tiles_per_split = c.tiles_per_split;
@@ -166,9 +173,9 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     if (e != cudaSuccess) return e;
     ++*launches;
     if (c.split > 1) {
-        e = mode == kModeComp    ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s)
-            : mode == kModeCheck ? reduce_check(P.part, c.split, P.n_act, acc, jerk, pot, s)
-                                 : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s);
+        e = mode == kModeComp    ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev)
+            : mode == kModeCheck ? reduce_check(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev)
+                                 : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev);
         if (e != cudaSuccess) return e;
         ++*launches;
     }

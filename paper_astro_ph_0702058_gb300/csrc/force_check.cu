@@ -11,9 +11,9 @@ cudaError_t force_dispatch_check(const ForceParams &P, const ForceConfig &cfg, c
 int force_occupancy_check(int threads, int ipt) { return force_occupancy<kModeCheck>(threads, ipt); }
 
 cudaError_t reduce_check(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
-                         cudaStream_t s)
+                         cudaStream_t s, const long long *n_act_dev)
 {
-    return reduce_launch<kModeCheck>(part, split, n_act, acc, jerk, pot, s);
+    return reduce_launch<kModeCheck>(part, split, n_act, acc, jerk, pot, s, n_act_dev);
 }
 
 }  // namespace nb

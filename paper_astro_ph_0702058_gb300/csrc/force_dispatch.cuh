@@ -89,16 +89,19 @@ int force_occupancy(int threads, int ipt)
     return 0;
 }
 
+// n_act sizes the launch; with n_act_dev the kernels read the actual (smaller
+// or equal) block size on the device.
 template <int MODE>
 cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, double *jerk,
-                          double *pot, cudaStream_t s)
+                          double *pot, cudaStream_t s, const long long *n_act_dev = nullptr)
 {
     const int nt = 256;
     if (split >= 32 && n_act <= 8192)
-        reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot);
+        reduce_partials_warp_kernel<MODE><<<(n_act + 7) / 8, nt, 0, s>>>(part, split, n_act, acc, jerk, pot,
+                                                                         n_act_dev);
     else
         reduce_partials_kernel<MODE><<<static_cast<unsigned>((7LL * n_act + nt - 1) / nt), nt, 0, s>>>(
-            part, split, n_act, acc, jerk, pot);
+            part, split, n_act, acc, jerk, pot, n_act_dev);
     return cudaGetLastError();
 }
 

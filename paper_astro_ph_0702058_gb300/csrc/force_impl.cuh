@@ -47,6 +47,8 @@ struct ForceParams {
     const float *__restrict__ soa;  // SoA j-stream (kSoaArrays x n_tiles * kJTile), or NULL
     const int32_t *__restrict__ active;
     int n_act;
+    const long long *n_act_dev;  // when set, the block size is read here on the device (graph replays);
+                                 // n_act then only bounds the launch
     int n;
     int n_tiles;
     int tiles_per_split;
@@ -346,9 +348,10 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
 template <int MODE>
 __global__ void reduce_partials_kernel(const float *__restrict__ part, int split, int n_act,
                                        double *__restrict__ acc, double *__restrict__ jerk,
-                                       double *__restrict__ pot)
+                                       double *__restrict__ pot, const long long *n_act_dev)
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
+    if (n_act_dev) n_act = static_cast<int>(*n_act_dev);
     const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (idx >= 7LL * n_act) return;
     const int c = static_cast<int>(idx / n_act);
@@ -373,9 +376,10 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
 template <int MODE>
 __global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int split, int n_act,
                                             double *__restrict__ acc, double *__restrict__ jerk,
-                                            double *__restrict__ pot)
+                                            double *__restrict__ pot, const long long *n_act_dev)
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
+    if (n_act_dev) n_act = static_cast<int>(*n_act_dev);
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= n_act) return;

@@ -11,9 +11,9 @@ cudaError_t force_dispatch_plain(const ForceParams &P, const ForceConfig &cfg, c
 int force_occupancy_plain(int threads, int ipt) { return force_occupancy<kModePlain>(threads, ipt); }
 
 cudaError_t reduce_plain(const float *part, int split, int n_act, double *acc, double *jerk, double *pot,
-                        cudaStream_t s)
+                         cudaStream_t s, const long long *n_act_dev)
 {
-    return reduce_launch<kModePlain>(part, split, n_act, acc, jerk, pot, s);
+    return reduce_launch<kModePlain>(part, split, n_act, acc, jerk, pot, s, n_act_dev);
 }
 
 }  // namespace nb

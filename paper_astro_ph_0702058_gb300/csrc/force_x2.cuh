@@ -211,6 +211,8 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     __shared__ __align__(128) SoaTile<MODE> soa[SOAIN ? 2 * TG : 1];
     __shared__ __align__(8) uint64_t bar[2];
 
+    const int n_act = P.n_act_dev ? static_cast<int>(*P.n_act_dev) : P.n_act;
+    if (static_cast<int>(blockIdx.x) * NT * IPT >= n_act) return;  // a launch sized for more rows
     const int tid = threadIdx.x;
     const int t_begin = blockIdx.y * P.tiles_per_split;
     const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
@@ -224,7 +226,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     for (int u = 0; u < IPT; ++u) {
         const int q = (blockIdx.x * IPT + u) * NT + tid;
         int idx = -1;
-        if (q < P.n_act) {
+        if (q < n_act) {
             idx = P.active[q];
             if (idx < 0 || idx >= P.n) {
                 atomicOr(&P.st->flags, kFlagBadIndex);
@@ -356,7 +358,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         const int q = (blockIdx.x * IPT + u) * NT + tid;
-        if (q >= P.n_act) continue;
+        if (q >= n_act) continue;
         if (gridDim.y == 1) {
             double r[7];
 #pragma unroll
@@ -374,11 +376,11 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             P.pot[q] = r[6];
         } else {
             constexpr int NC = (MODE == kModeComp) ? 14 : 7;
-            float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * P.n_act + q;
+            float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * n_act + q;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
-                base[static_cast<size_t>(c) * P.n_act] = tot[u][c];
-                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * P.n_act] = lo[u][c];
+                base[static_cast<size_t>(c) * n_act] = tot[u][c];
+                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * n_act] = lo[u][c];
             }
         }
     }

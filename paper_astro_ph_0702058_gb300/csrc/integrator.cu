@@ -21,8 +21,10 @@ int blocks_for(int64_t n, int threads, int cap = 1 << 20)
     return static_cast<int>(b < cap ? b : cap);
 }
 
-__global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int lo_parts)
+__global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int lo_parts,
+                               const long long *t_dev)
 {
+    if (t_dev) t_new = *t_dev;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const double dt = static_cast<double>(t_new - S.t[i]) * tick;
@@ -68,8 +70,12 @@ __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, do
 __global__ void correct_kernel(const State S, const int32_t *__restrict__ active, int64_t n_act,
                                const double *__restrict__ acc, const double *__restrict__ jerk,
                                int64_t t_new, double tick, double eta, int lmin, int lmax,
-                               DevStatus *st)
+                               DevStatus *st, const SchedOut *sched_dev)
 {
+    if (sched_dev) {
+        t_new = sched_dev->t_blk;
+        n_act = sched_dev->n_act;
+    }
     const int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (q >= n_act) return;
     const int64_t i = active[q];
@@ -348,23 +354,23 @@ cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches
 }
 
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
-                           cudaStream_t s, int64_t *launches)
+                           cudaStream_t s, int64_t *launches, const long long *t_dev)
 {
     predict_kernel<<<blocks_for(S.n, kThreads, 152 * 64), kThreads, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
-                                                                           lo_parts);
+                                                                           lo_parts, t_dev);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act, const double *acc,
                            const double *jerk, int64_t t_new, double eta, int lmin, int lmax, DevStatus *st,
-                           cudaStream_t s, int64_t *launches)
+                           cudaStream_t s, int64_t *launches, const SchedOut *sched_dev)
 {
     if (n_act <= 0) return cudaSuccess;
     // FP64-heavy rows: small blocks spread over more SMs (GB300's FP64 rate per SM is low)
     const int tpb = n_act >= 152 * 128 ? 128 : 32;
     correct_kernel<<<blocks_for(n_act, tpb), tpb, 0, s>>>(S, active, n_act, acc, jerk, t_new, ldexp(1.0, -lmax),
-                                                          eta, lmin, lmax, st);
+                                                          eta, lmin, lmax, st, sched_dev);
     ++*launches;
     return cudaGetLastError();
 }

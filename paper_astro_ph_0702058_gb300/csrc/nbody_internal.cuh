@@ -89,14 +89,18 @@ extern int g_skip_first_copy;  // test hook: force kernels leave out their first
 // req_* > 0 override the automatic choice.
 int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_threads,
                  int req_ipt, int req_split, ForceConfig *cfg);
+// Whether this mode's force kernels honour ForceParams::n_act_dev (the packed kernels).
+bool force_reads_device_rows(int mode);
 // Scratch bytes needed for partial sums when cfg.split > 1 (0 otherwise).
 size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act);
 // Launches the force evaluation (and the fixed-order partial reduction when
-// split > 1).  acc/jerk: n_act*3, pot: n_act, device doubles.
+// split > 1).  acc/jerk: n_act*3, pot: n_act, device doubles.  With n_act_dev
+// (packed plain/compensated kernels only) the launch is sized for n_act rows
+// and the kernels read the actual block size from *n_act_dev on the device.
 cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active,
                          int64_t n_act, double eps2, const ForceConfig &cfg, double *acc,
                          double *jerk, double *pot, void *partials, DevStatus *st,
-                         cudaStream_t s, int64_t *launches);
+                         cudaStream_t s, int64_t *launches, const long long *n_act_dev = nullptr);
 
 // ---- force_ds.cu ----
 int force_occupancy_ds();
@@ -110,11 +114,14 @@ cudaError_t force_sorted_launch(const JStream &js, int64_t n, const int32_t *act
                                 double *acc, double *jerk, double *pot, DevStatus *st, cudaStream_t s);
 
 // ---- integrator.cu ----
+struct SchedOut;
+// t_dev / sched_dev (graph replays): the time and block size are read on the device.
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
-                           cudaStream_t s, int64_t *launches);
+                           cudaStream_t s, int64_t *launches, const long long *t_dev = nullptr);
 cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act,
                            const double *acc, const double *jerk, int64_t t_new, double eta,
-                           int lmin, int lmax, DevStatus *st, cudaStream_t s, int64_t *launches);
+                           int lmin, int lmax, DevStatus *st, cudaStream_t s, int64_t *launches,
+                           const SchedOut *sched_dev = nullptr);
 // a, k <- the full force at t = 0 (acc, jerk: n*3), t <- 0, level from Eq. (initTimestep).
 cudaError_t init_levels_launch(const State &S, const double *acc, const double *jerk,
                                double eta_init, int lmin, int lmax, DevStatus *st,
