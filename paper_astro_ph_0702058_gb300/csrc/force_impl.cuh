@@ -33,7 +33,7 @@
 #define NB_JUNROLL 8
 #endif
 #ifndef NB_FOLD
-#define NB_FOLD 64
+#define NB_FOLD 128
 #endif
 
 namespace nb {

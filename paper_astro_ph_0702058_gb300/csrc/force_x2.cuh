@@ -14,7 +14,7 @@
 //   - the pair term of Appendix A runs on packed operands, with the MUFU
 //     reciprocal square root applied to each half;
 //   - the two halves hold partial sums of the even and odd j of a fold; they
-//     are added at each 64-pair fold, then folded into the running total as in
+//     are added at each fold (NB_FOLD pairs), then folded into the running total as in
 //     the scalar kernel (FP32 add, or TwoSum into double-single).
 #pragma once
 

@@ -15,7 +15,7 @@ FP64 from the particles' positions and velocities:
   pair arithmetic: the MUFU reciprocal square root (relative error <= 2^-22.9,
       about 2.1 u, entering r^-3 three times and r^-5 five times) plus the
       roundings of the products and fused multiply-adds: C_ARITH u |term|;
-  summation: FP32 partial sums of FOLD = 64 terms, then FP32 additions of the
+  summation: FP32 partial sums of FOLD = 128 terms, then FP32 additions of the
       partials (plain) or double-single folds (compensated): a statistical
       bound C_SUM u (sqrt(FOLD) + sqrt(n_partials)) sum_j |term| with the
       second root absent in compensated mode.
@@ -30,7 +30,7 @@ import math
 import numpy as np
 
 U = 2.0 ** -24
-FOLD = 64
+FOLD = 128  # pairs per FP32 partial sum in the force kernels
 C_ARITH = {"acc": 10.0, "jerk": 24.0, "pot": 6.0}
 C_SUM = 2.0
 

@@ -75,7 +75,7 @@ def test_sumcheck_sums_equal_exact_sums_of_fp32_terms(torch, n, n_act, shape):
 
 
 def test_production_comp_differs_only_by_term_rounding(torch):
-    """The production compensated mode (hardware rsqrt, 64-term FP32 partials) sits at FP32
+    """The production compensated mode (hardware rsqrt, 128-term FP32 partials) sits at FP32
     term-rounding distance from the same exact sums, far above the summation-check mode."""
     from paper_astro_ph_0702058_gb300 import Simulation
     n = 4099
