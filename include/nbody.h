@@ -218,7 +218,8 @@ typedef struct {
     int last_i_per_thread;
     int last_j_split;
     int mode;
-    int64_t graph_blocks;  /* block steps nbody_step ran as one replayed CUDA graph */
+    int64_t graph_blocks;  /* block steps nbody_step ran inside a replayed CUDA graph */
+    int64_t loop_blocks;   /* of those, the ones the device-side loop added (no host round trip) */
 } nbody_stats;
 
 int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);
@@ -243,13 +244,20 @@ void nbody_debug_fail_alloc(int k);
  * the context stays usable.  Exercises the failure path of the device waits. */
 void nbody_debug_skip_tile_copy(int on);
 
-/* Test switch (default on): nbody_step replays blocks small enough for one
- * captured CUDA graph (predictor, force, corrector, the next block's schedule
- * and its read-back, reading the block time and size on the device) instead
- * of launching each kernel from the host.  The graph is used only when its
- * launch shape is the one the separate launches would take, so both give the
- * same results bit for bit; off (0) forces the separate launches. */
-void nbody_debug_step_graphs(int on);
+/* Test switch for how nbody_step runs blocks small enough for one captured
+ * CUDA graph (predictor, force, corrector, the next block's schedule, reading
+ * the block time and size on the device):
+ *   0  separate launches from the host for every block;
+ *   1  one graph replay per block, then the host reads the next block back;
+ *   2  (default) the block step is the body of a device-side loop (a while-node
+ *      of the graph): after each block a one-thread kernel runs the next one in
+ *      the same replay while it is due by t_end, takes the graph's launch shape,
+ *      no error flag is raised and at most 1024 blocks have run; the host then
+ *      reads back the next block.  Without while-nodes it acts as 1.
+ * The graph is used only when its launch shape is the one the separate
+ * launches would take, so all three give the same results bit for bit.
+ * Values outside 0..2 are clamped. */
+void nbody_debug_step_graphs(int level);
 
 /* ------------------------------------------------------------ differentiation
  * Reverse mode of a shared-step rollout: the force of Eq. (Force) at t = 0,

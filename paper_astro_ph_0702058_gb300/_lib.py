@@ -55,7 +55,8 @@ class nbody_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_pad", C.c_int64), ("blocks", C.c_int64), ("below_dt_min", C.c_int64),
                 ("nonfinite", C.c_int64), ("force_calls", C.c_int64), ("pairs", C.c_int64),
                 ("kernel_launches", C.c_int64), ("last_threads", C.c_int), ("last_i_per_thread", C.c_int),
-                ("last_j_split", C.c_int), ("mode", C.c_int), ("graph_blocks", C.c_int64)]
+                ("last_j_split", C.c_int), ("mode", C.c_int), ("graph_blocks", C.c_int64),
+                ("loop_blocks", C.c_int64)]
 
 
 class NBodyError(RuntimeError):
@@ -274,8 +275,9 @@ def nbody_debug_skip_tile_copy(on: bool) -> None:
     lib().nbody_debug_skip_tile_copy(1 if on else 0)
 
 
-def nbody_debug_step_graphs(on: bool) -> None:
-    lib().nbody_debug_step_graphs(1 if on else 0)
+def nbody_debug_step_graphs(level: int) -> None:
+    """0: separate launches, 1: one graph replay per block, 2 (default): device-side block loop."""
+    lib().nbody_debug_step_graphs(int(level))
 
 
 def nbody_force_noalloc(posm, vel, poslo, n: int, active, n_act: int, eps2: float, mode: int,

@@ -20,7 +20,10 @@ namespace {
 
 thread_local char g_err[512] = "";
 int g_fail_alloc = 0;    // allocation-failure injection countdown (test hook)
-int g_step_graphs = 1;   // nbody_step replays small blocks as a CUDA graph (test switch)
+// nbody_step's small blocks (test switch): 0 separate launches, 1 one graph
+// replay per block, 2 a device-side loop of blocks in each replay
+int g_step_graphs = 2;
+constexpr int64_t kLoopCap = 1024;  // blocks one replay of the loop may run
 
 int fail(int code, const char *fmt, ...)
 {
@@ -110,12 +113,18 @@ struct nbody_ctx {
     int64_t t_max = 0;      // largest t_i (ticks)
     int64_t t_pred = 0;     // time of the last prediction (ticks)
     // nbody_step's small-block graph: predict, force, correct, schedule the next block and read
-    // it back, all sized for graph_rows rows and reading the block time and size on the device
+    // it back, all sized for graph_rows rows and reading the block time and size on the device;
+    // with graph_loop the block step is the body of a while-node that repeats it on the device
+    // while the next block fits (graph_fits) and the loop control (loop_dev) allows
     cudaGraphExec_t step_graph = nullptr;
     int64_t graph_rows = 0;
     ForceConfig graph_cfg{};
     void *graph_partials = nullptr;
-    int64_t graph_launches = 0;  // kernel nodes per replay
+    int64_t graph_launches = 0;  // kernel nodes per block step of a replay
+    bool graph_loop = false;
+    unsigned char *graph_fits = nullptr;  // graph_rows + 1 flags: block size na takes the graph's shape
+    StepLoop *loop_dev = nullptr;
+    StepLoop *loop_host = nullptr;
     bool pred_valid = false;
     int64_t force_n_act = -1;
     nbody_stats stats{};
@@ -128,10 +137,10 @@ void release(nbody_ctx *c)
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     void *dev[] = {c->state, c->t, c->level, c->jbuf, c->act_force, c->act_corr, c->act_sched,
                    c->f_acc, c->f_jerk, c->f_pot, c->stage, c->partials, c->sched_scratch,
-                   c->sched_out, c->st, c->phi, c->e_out, c->trange};
+                   c->sched_out, c->st, c->phi, c->e_out, c->trange, c->graph_fits, c->loop_dev};
     for (void *d : dev)
         if (d) cudaFree(d);
-    void *host[] = {c->sched_host, c->st_host, c->e_host, c->trange_host};
+    void *host[] = {c->sched_host, c->st_host, c->e_host, c->trange_host, c->loop_host};
     for (void *h : host)
         if (h) cudaFreeHost(h);
     delete c;
@@ -359,6 +368,8 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     NB_INIT(host_alloc(reinterpret_cast<void **>(&c->e_host), 2 * sizeof(double)), "pinned allocation");
     NB_INIT(host_alloc(reinterpret_cast<void **>(&c->trange_host), 2 * sizeof(unsigned long long)),
             "pinned allocation");
+    NB_INIT(dev_alloc(reinterpret_cast<void **>(&c->loop_dev), sizeof(StepLoop)), "loop control allocation");
+    NB_INIT(host_alloc(reinterpret_cast<void **>(&c->loop_host), sizeof(StepLoop)), "pinned allocation");
     std::memset(c->st_host, 0, sizeof(DevStatus));
 
     State &S = c->S;
@@ -509,6 +520,107 @@ bool same_shape(const ForceConfig &a, const ForceConfig &b)
     return a.threads == b.threads && a.ipt == b.ipt && a.split == b.split && a.tiles_per_split == b.tiles_per_split;
 }
 
+// One block step sized for graph_rows rows, captured on cs: predictor, force,
+// corrector and the next block's schedule, all reading the block time and size
+// on the device.
+cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches)
+{
+    const int64_t rows = c->graph_rows;
+    cudaError_t e = predict_launch(c->S, c->J, 0, c->p.lmax, predict_lo_parts(c->p.mode), cs, launches,
+                                   &c->sched_out->t_blk);
+    if (e == cudaSuccess)
+        e = force_launch(c->p.mode, c->J, c->n, c->act_sched, rows, c->eps2, c->graph_cfg, c->f_acc, c->f_jerk,
+                         c->f_pot, c->partials, c->st, cs, launches, &c->sched_out->n_act);
+    if (e == cudaSuccess)
+        e = correct_launch(c->S, c->act_sched, rows, c->f_acc, c->f_jerk, 0, c->p.eta, c->p.lmin, c->p.lmax, c->st,
+                           cs, launches, c->sched_out);
+    if (e == cudaSuccess) e = schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, launches);
+    return e;
+}
+
+// Status flags that end the device-side loop: every error flag, and the dt_min
+// clamp in strict mode (the flags the host would report after that block).
+unsigned loop_stop_flags(const nbody_ctx *c)
+{
+    return kFlagTimeout | kFlagBadIndex | kFlagNonfinite | (c->p.strict ? kFlagDtMin : 0u);
+}
+
+// Builds the replayed graph: the block step as the body of a while-node, whose
+// last kernel decides whether the next block runs in the same replay, then the
+// read-back of the next block, the status and the loop control.  Without
+// while-nodes (loop = false) the graph holds one block step.
+cudaError_t capture_step_graph(nbody_ctx *c, bool loop, cudaGraph_t *out, int64_t *launches)
+{
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t loop_node = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaGraphConditionalHandle h{};
+    e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess && loop) {
+        e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&loop_node, g, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    cudaGraph_t captured = nullptr;
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cs, loop ? body : g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = capture_block_step(c, cs, launches);
+        if (e2 == cudaSuccess && loop)
+            e2 = step_loop_launch(h, c->sched_out, c->graph_fits, c->graph_rows + 1, c->st, loop_stop_flags(c),
+                                  c->loop_dev, cs, launches);
+        if (e2 == cudaSuccess && !loop) e2 = cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut),
+                                                              cudaMemcpyDeviceToHost, cs);
+        if (e2 == cudaSuccess && !loop)
+            e2 = cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, cs);
+        e = cudaStreamEndCapture(cs, &captured);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && loop) {
+        e = cudaStreamBeginCaptureToGraph(cs, g, &loop_node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, cs);
+            if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, cs);
+            if (e2 == cudaSuccess)
+                e2 = cudaMemcpyAsync(c->loop_host, c->loop_dev, sizeof(StepLoop), cudaMemcpyDeviceToHost, cs);
+            e = cudaStreamEndCapture(cs, &captured);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
+// Fills graph_fits: flag na is set when a block of na rows takes the graph's
+// launch shape, the test the host applies before a replay.
+int set_graph_fits(nbody_ctx *c)
+{
+    const int64_t len = c->graph_rows + 1;
+    std::vector<unsigned char> fits(static_cast<size_t>(len), 0);
+    for (int64_t na = 1; na < len; ++na) {
+        ForceConfig cfg{};
+        fits[na] = force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
+                                &cfg) == NBODY_OK && same_shape(cfg, c->graph_cfg);
+    }
+    NB_CUDA(dev_alloc(reinterpret_cast<void **>(&c->graph_fits), static_cast<size_t>(len)), "graph table allocation");
+    NB_CUDA(cudaMemcpy(c->graph_fits, fits.data(), static_cast<size_t>(len), cudaMemcpyHostToDevice),
+            "graph table upload");
+    return NBODY_OK;
+}
+
 // Captures the graph once (and again when the partial-sum scratch moved).
 int build_step_graph(nbody_ctx *c)
 {
@@ -517,41 +629,35 @@ int build_step_graph(nbody_ctx *c)
         cudaGraphExecDestroy(c->step_graph);
         c->step_graph = nullptr;
     }
-    const int64_t rows = c->graph_rows;
-    const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, c->graph_cfg, rows));
+    const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, c->graph_cfg, c->graph_rows));
     if (rp != NBODY_OK) return rp;
-    cudaStream_t cs = nullptr;
-    NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    if (!c->graph_fits) {
+        const int rf = set_graph_fits(c);
+        if (rf != NBODY_OK) return rf;
+    }
     int64_t launches = 0;
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t e2 = predict_launch(c->S, c->J, 0, c->p.lmax, predict_lo_parts(c->p.mode), cs, &launches,
-                                        &c->sched_out->t_blk);
-        if (e2 == cudaSuccess)
-            e2 = force_launch(c->p.mode, c->J, c->n, c->act_sched, rows, c->eps2, c->graph_cfg, c->f_acc, c->f_jerk,
-                              c->f_pot, c->partials, c->st, cs, &launches, &c->sched_out->n_act);
-        if (e2 == cudaSuccess)
-            e2 = correct_launch(c->S, c->act_sched, rows, c->f_acc, c->f_jerk, 0, c->p.eta, c->p.lmin, c->p.lmax,
-                                c->st, cs, &launches, c->sched_out);
-        if (e2 == cudaSuccess)
-            e2 = schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, &launches);
-        if (e2 == cudaSuccess)
-            e2 = cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, cs);
-        if (e2 == cudaSuccess)
-            e2 = cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, cs);
-        e = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = e2;
-    }
+    bool loop = true;
+    cudaError_t e = capture_step_graph(c, true, &g, &launches);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    if (e != cudaSuccess) {  // no while-nodes: one block step per replay
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        g = nullptr;
+        c->step_graph = nullptr;
+        loop = false;
+        launches = 0;
+        e = capture_step_graph(c, false, &g, &launches);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    }
     if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         c->step_graph = nullptr;
         return cuda_fail(e, "step graph capture");
     }
     c->graph_partials = c->partials;
     c->graph_launches = launches;
+    c->graph_loop = loop;
     return NBODY_OK;
 }
 
@@ -568,9 +674,10 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     if (tend < c->t_max) return fail(NBODY_EINVAL, "nbody_step: t_end is before the current time");
     int64_t done = 0;
     // Small blocks replay one graph (predict, force, correct, next schedule and its read-back) when its
-    // launch shape is the one the separate launches would take, so both give the same bits.
+    // launch shape is the one the separate launches would take, so both give the same bits; inside a
+    // replay a device-side loop runs the following blocks while they fit too.
     const bool packed = force_reads_device_rows(c->p.mode);
-    if (g_step_graphs && packed && c->graph_rows == 0) {
+    if (g_step_graphs > 0 && packed && c->graph_rows == 0) {
         c->graph_rows = graph_rows_for(c);
         if (force_choose(c->p.mode, c->graph_rows, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
                          &c->graph_cfg) != NBODY_OK)
@@ -580,28 +687,43 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     r = schedule_internal(c, &tb, &na);
     while (r == NBODY_OK && tb <= tend && !(max_steps > 0 && done >= max_steps)) {
         ForceConfig cfg{};
-        bool use_graph = g_step_graphs && packed && c->graph_rows > 0 && na <= c->graph_rows &&
+        bool use_graph = g_step_graphs > 0 && packed && c->graph_rows > 0 && na <= c->graph_rows &&
                          force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block,
                                       c->p.j_split, &cfg) == NBODY_OK &&
                          same_shape(cfg, c->graph_cfg);
         if (use_graph) {
             r = build_step_graph(c);
             if (r != NBODY_OK) break;
+            StepLoop *L = c->loop_host;
+            if (c->graph_loop) {  // the first block is this one; the loop may add up to `budget` more
+                const int64_t left = max_steps > 0 ? max_steps - done - 1 : kLoopCap;
+                L->t_end = tend;
+                L->budget = g_step_graphs >= 2 ? std::min(left, kLoopCap) : 0;
+                L->blocks = 0;
+                L->rows = 0;
+                L->last_t = tb;
+                NB_CUDA(cudaMemcpyAsync(c->loop_dev, L, sizeof(StepLoop), cudaMemcpyHostToDevice, c->s),
+                        "loop control upload");
+            }
             NB_CUDA(cudaGraphLaunch(c->step_graph, c->s), "step graph launch");
             NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
-            c->stats.kernel_launches += c->graph_launches;
-            c->stats.force_calls += 1;
-            c->stats.pairs += na * (c->n - 1);
-            c->stats.blocks += 1;
-            c->stats.graph_blocks += 1;
+            const int64_t more = c->graph_loop ? L->blocks : 0;
+            const int64_t last_t = c->graph_loop ? L->last_t : tb;
+            const int64_t rows = na + (c->graph_loop ? L->rows : 0);
+            c->stats.kernel_launches += (1 + more) * c->graph_launches;
+            c->stats.force_calls += 1 + more;
+            c->stats.pairs += rows * (c->n - 1);
+            c->stats.blocks += 1 + more;
+            c->stats.graph_blocks += 1 + more;
+            c->stats.loop_blocks += more;
             c->stats.last_threads = cfg.threads;
             c->stats.last_i_per_thread = cfg.ipt;
             c->stats.last_j_split = cfg.split;
-            c->t_max = std::max(c->t_max, tb);
-            c->t_pred = tb;
+            c->t_max = std::max(c->t_max, last_t);
+            c->t_pred = last_t;
             c->pred_valid = false;
             c->force_n_act = -1;
-            ++done;
+            done += 1 + more;
             r = absorb_status(c);
             if (r != NBODY_OK) break;
             tb = c->sched_host->t_blk;
@@ -887,6 +1009,6 @@ void nbody_debug_fail_alloc(int k) { g_fail_alloc = k > 0 ? k : 0; }
 
 void nbody_debug_skip_tile_copy(int on) { nb::g_skip_first_copy = on ? 1 : 0; }
 
-void nbody_debug_step_graphs(int on) { g_step_graphs = on ? 1 : 0; }
+void nbody_debug_step_graphs(int level) { g_step_graphs = level < 0 ? 0 : (level > 2 ? 2 : level); }
 
 }  // extern "C"

@@ -214,6 +214,58 @@ __global__ void sched_write_kernel(const State S, int lmax, int64_t chunk, int n
     }
 }
 
+// n <= one chunk: the three passes in one block and one launch (same list).
+constexpr int kSchedSingleThreads = 1024;
+
+__global__ void sched_single_kernel(const State S, int lmax, SchedOut *out, int32_t *active)
+{
+    __shared__ unsigned long long shm[32];
+    __shared__ int warp_tot[32];
+    unsigned long long m = ~0ull;
+    for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) {
+        const unsigned long long d = due_tick(S, i, lmax);
+        m = d < m ? d : m;
+    }
+    const unsigned long long g = block_reduce(m, MinOp(), shm, ~0ull);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    long long off = 0;
+    for (int64_t base = 0; base < S.n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool hit = i < S.n && due_tick(S, i, lmax) == g;
+        const unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (l == 0) warp_tot[w] = __popc(mask);
+        __syncthreads();
+        int before = 0, round = 0;
+        for (int k = 0; k < nw; ++k) {
+            if (k < w) before += warp_tot[k];
+            round += warp_tot[k];
+        }
+        if (hit) active[off + before + __popc(mask & ((1u << l) - 1u))] = static_cast<int32_t>(i);
+        off += round;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->t_blk = static_cast<long long>(g);
+        out->n_act = off;
+    }
+}
+
+// One thread: decides whether the device-side block loop runs another block.
+__global__ void step_loop_kernel(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
+                                 long long n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L)
+{
+    const long long t = next->t_blk, na = next->n_act;
+    const bool go = L->budget > 0 && (st->flags & stop_flags) == 0u && t <= L->t_end && na > 0 && na < n_fits &&
+                    fits[na] != 0;
+    if (go) {
+        L->budget -= 1;
+        L->blocks += 1;
+        L->rows += na;
+        L->last_t = t;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------ energy
 // phi_i = -sum_{j != i} m_j / sqrt(r^2 + eps^2) in FP64, j in ascending order.
 constexpr int kETile = 128;
@@ -393,12 +445,26 @@ cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut 
                             cudaStream_t s, int64_t *launches)
 {
     const SchedGeom g = sched_geom(S.n);
+    if (g.blocks == 1) {
+        sched_single_kernel<<<1, kSchedSingleThreads, 0, s>>>(S, lmax, out, active);
+        ++*launches;
+        return cudaGetLastError();
+    }
     unsigned long long *bmin = static_cast<unsigned long long *>(scratch);
     long long *bcnt = reinterpret_cast<long long *>(bmin + g.blocks);
     sched_min_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, bmin);
     sched_count_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, g.blocks, bmin, bcnt, out);
     sched_write_kernel<<<g.blocks, kThreads, 0, s>>>(S, lmax, g.chunk, g.blocks, bcnt, out, active);
     *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t step_loop_launch(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
+                             int64_t n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L,
+                             cudaStream_t s, int64_t *launches)
+{
+    step_loop_kernel<<<1, 1, 0, s>>>(h, next, fits, n_fits, st, stop_flags, L);
+    ++*launches;
     return cudaGetLastError();
 }
 

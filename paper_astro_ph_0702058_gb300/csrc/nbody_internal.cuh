@@ -136,6 +136,23 @@ size_t sched_scratch_bytes(int64_t n);
 cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut *out,
                             void *scratch, cudaStream_t s, int64_t *launches);
 
+// Control block of a device-side loop over block steps (a while-node of a CUDA
+// graph whose body is one block step): the host sets t_end, budget and last_t
+// before a launch and reads blocks, rows and last_t after it.
+struct StepLoop {
+    long long t_end;   // ticks: a block due later does not run
+    long long budget;  // blocks the loop may still add in this launch
+    long long blocks;  // blocks it added
+    long long rows;    // their active rows
+    long long last_t;  // block time of the last block that ran
+};
+// Last node of the loop body: the next block (scheduled in `next`) runs when
+// no flag of stop_flags is raised in st, it is due by t_end, its size na has
+// 0 < na < n_fits and fits[na] != 0, and budget is left; sets the condition.
+cudaError_t step_loop_launch(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
+                             int64_t n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L,
+                             cudaStream_t s, int64_t *launches);
+
 // E_kin and E_pot (phi scratch: n doubles; out: 2 doubles).
 cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, double *out,
                           cudaStream_t s, int64_t *launches);

@@ -1,4 +1,5 @@
-"""nbody_step's small-block CUDA graph: the same bits as separate launches, and it is used."""
+"""nbody_step's small-block CUDA graph, one block per replay or a device-side loop of blocks per
+replay: the same bits as separate launches, and both are used."""
 import numpy as np
 import pytest
 
@@ -13,33 +14,52 @@ def torch():
     return need_gpu()
 
 
-def _run(m, x, v, mode, t_end, eta, graphs):
+def _run(m, x, v, mode, t_end, eta, graphs, max_steps=0):
     from paper_astro_ph_0702058_gb300 import Simulation, nbody_debug_step_graphs
     nbody_debug_step_graphs(graphs)
     try:
         with Simulation(m, x, v, EPS2, eta=eta, lmin=6, lmax=26, mode=mode) as sim:
-            nb = sim.step(t_end)
+            nb = sim.step(t_end, max_steps)
             n = len(m)
             out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), a=np.zeros((n, 3)), k=np.zeros((n, 3)),
                        t_tick=np.zeros(n, dtype=np.int64), level=np.zeros(n, dtype=np.int8))
             sim.get_state(**out)
             st = sim.stats()
-            e = sum(sim.energy())
+            e = sum(sim.energy()) if max_steps == 0 else None  # energy needs synchronised particles
     finally:
-        nbody_debug_step_graphs(True)
+        nbody_debug_step_graphs(2)
     return nb, out, st, e
 
 
 @pytest.mark.parametrize("mode", ["plain", "comp"])
-@pytest.mark.parametrize("n,t_end,eta", [(1024, 0.125, 0.01), (4099, 1.0 / 64, 0.02), (65536, 1.0 / 64, 0.02)])
+# (1024, 1.0, 0.01) runs ~3000 blocks: replays of the device loop end at its cap of 1024 blocks
+@pytest.mark.parametrize("n,t_end,eta", [(1024, 0.125, 0.01), (1024, 1.0, 0.01), (4099, 1.0 / 64, 0.02),
+                                         (65536, 1.0 / 64, 0.02)])
 def test_graph_blocks_equal_separate_launches(torch, mode, n, t_end, eta):
     m, x, v = plummer_sphere(n, 70 + n % 13)
-    nb_g, s_g, st_g, e_g = _run(m, x, v, mode, t_end, eta, True)
-    nb_s, s_s, st_s, e_s = _run(m, x, v, mode, t_end, eta, False)
-    assert nb_g == nb_s and st_g["pairs"] == st_s["pairs"] and st_g["blocks"] == st_s["blocks"]
+    nb_s, s_s, st_s, e_s = _run(m, x, v, mode, t_end, eta, 0)
+    assert st_s["graph_blocks"] == 0 and st_s["loop_blocks"] == 0
+    for level in (1, 2):
+        nb_g, s_g, st_g, e_g = _run(m, x, v, mode, t_end, eta, level)
+        assert nb_g == nb_s and st_g["pairs"] == st_s["pairs"] and st_g["blocks"] == st_s["blocks"], level
+        for key in s_g:
+            assert np.array_equal(s_g[key], s_s[key]), (level, key)
+        assert e_g == e_s, level
+        assert st_g["graph_blocks"] > 0  # small blocks went through the graph
+        if level == 1:
+            assert st_g["loop_blocks"] == 0
+        else:  # most graph blocks ran without a host round trip
+            assert st_g["loop_blocks"] > 0
+        print(f"\nn={n} {mode} level {level}: {nb_g} blocks, {st_g['graph_blocks']} in graph replays, "
+              f"{st_g['loop_blocks']} added by the device loop")
+
+
+@pytest.mark.parametrize("max_steps", [1, 7, 300])
+def test_device_loop_honours_max_steps(torch, max_steps):
+    """The device loop stops after exactly max_steps blocks, as the host loop does."""
+    m, x, v = plummer_sphere(1024, 5)
+    nb_s, s_s, st_s, _ = _run(m, x, v, "plain", 0.125, 0.01, 0, max_steps)
+    nb_g, s_g, st_g, _ = _run(m, x, v, "plain", 0.125, 0.01, 2, max_steps)
+    assert nb_s == nb_g == max_steps and st_g["blocks"] == max_steps
     for key in s_g:
         assert np.array_equal(s_g[key], s_s[key]), key
-    assert e_g == e_s
-    assert st_s["graph_blocks"] == 0
-    assert st_g["graph_blocks"] > 0  # small blocks went through the graph
-    print(f"\nn={n} {mode}: {nb_g} blocks, {st_g['graph_blocks']} as graph replays")
