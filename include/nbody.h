@@ -250,10 +250,14 @@ void nbody_debug_skip_tile_copy(int on);
  *   0  separate launches from the host for every block;
  *   1  one graph replay per block, then the host reads the next block back;
  *   2  (default) the block step is the body of a device-side loop (a while-node
- *      of the graph): after each block a one-thread kernel runs the next one in
- *      the same replay while it is due by t_end, takes the graph's launch shape,
- *      no error flag is raised and at most 1024 blocks have run; the host then
- *      reads back the next block.  Without while-nodes it acts as 1.
+ *      of the graph): after each block's schedule one thread lets the next
+ *      block run in the same replay while it is due by t_end, takes the
+ *      graph's launch shape, no error flag is raised and at most 1024 blocks
+ *      have run; the host then reads back the next block.  Without while-nodes
+ *      it acts as 1.
+ * A context captures its graph in the form of the level in force when it
+ * builds it (once, and again only if its scratch buffer moves); a loop graph
+ * run at level 1 stops after each block.
  * The graph is used only when its launch shape is the one the separate
  * launches would take, so all three give the same results bit for bit.
  * Values outside 0..2 are clamped. */

@@ -522,8 +522,8 @@ bool same_shape(const ForceConfig &a, const ForceConfig &b)
 
 // One block step sized for graph_rows rows, captured on cs: predictor, force,
 // corrector and the next block's schedule, all reading the block time and size
-// on the device.
-cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches)
+// on the device; with la, the loop's decision after the schedule.
+cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches, const LoopArgs *la)
 {
     const int64_t rows = c->graph_rows;
     cudaError_t e = predict_launch(c->S, c->J, 0, c->p.lmax, predict_lo_parts(c->p.mode), cs, launches,
@@ -534,7 +534,9 @@ cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches)
     if (e == cudaSuccess)
         e = correct_launch(c->S, c->act_sched, rows, c->f_acc, c->f_jerk, 0, c->p.eta, c->p.lmin, c->p.lmax, c->st,
                            cs, launches, c->sched_out);
-    if (e == cudaSuccess) e = schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, launches);
+    if (e == cudaSuccess)
+        e = la ? schedule_loop_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, *la, cs, launches)
+               : schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, launches);
     return e;
 }
 
@@ -573,10 +575,8 @@ cudaError_t capture_step_graph(nbody_ctx *c, bool loop, cudaGraph_t *out, int64_
     if (e == cudaSuccess)
         e = cudaStreamBeginCaptureToGraph(cs, loop ? body : g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t e2 = capture_block_step(c, cs, launches);
-        if (e2 == cudaSuccess && loop)
-            e2 = step_loop_launch(h, c->sched_out, c->graph_fits, c->graph_rows + 1, c->st, loop_stop_flags(c),
-                                  c->loop_dev, cs, launches);
+        const LoopArgs la{h, c->graph_fits, c->graph_rows + 1, c->st, loop_stop_flags(c), c->loop_dev};
+        cudaError_t e2 = capture_block_step(c, cs, launches, loop ? &la : nullptr);
         if (e2 == cudaSuccess && !loop) e2 = cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut),
                                                               cudaMemcpyDeviceToHost, cs);
         if (e2 == cudaSuccess && !loop)
@@ -637,10 +637,10 @@ int build_step_graph(nbody_ctx *c)
     }
     int64_t launches = 0;
     cudaGraph_t g = nullptr;
-    bool loop = true;
-    cudaError_t e = capture_step_graph(c, true, &g, &launches);
+    bool loop = g_step_graphs >= 2;  // the form is fixed when a context first builds its graph
+    cudaError_t e = capture_step_graph(c, loop, &g, &launches);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, g, 0);
-    if (e != cudaSuccess) {  // no while-nodes: one block step per replay
+    if (e != cudaSuccess && loop) {  // no while-nodes: one block step per replay
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
         g = nullptr;

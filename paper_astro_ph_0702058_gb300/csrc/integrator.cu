@@ -214,10 +214,27 @@ __global__ void sched_write_kernel(const State S, int lmax, int64_t chunk, int n
     }
 }
 
-// n <= one chunk: the three passes in one block and one launch (same list).
+// Decision of the device-side block loop on the scheduled block (t, na); one thread.
+__device__ __forceinline__ void loop_decide(const LoopArgs &la, long long t, long long na)
+{
+    StepLoop *L = la.L;
+    const bool go = L->budget > 0 && (la.st->flags & la.stop_flags) == 0u && t <= L->t_end && na > 0 &&
+                    na < la.n_fits && la.fits[na] != 0;
+    if (go) {
+        L->budget -= 1;
+        L->blocks += 1;
+        L->rows += na;
+        L->last_t = t;
+    }
+    cudaGraphSetConditional(la.h, go ? 1u : 0u);
+}
+
+// n <= one chunk: the three passes in one block and one launch (same list);
+// inside the block loop (LOOP) thread 0 then takes the loop's decision.
 constexpr int kSchedSingleThreads = 1024;
 
-__global__ void sched_single_kernel(const State S, int lmax, SchedOut *out, int32_t *active)
+template <bool LOOP>
+__global__ void sched_single_kernel(const State S, int lmax, SchedOut *out, int32_t *active, const LoopArgs la)
 {
     __shared__ unsigned long long shm[32];
     __shared__ int warp_tot[32];
@@ -247,23 +264,14 @@ __global__ void sched_single_kernel(const State S, int lmax, SchedOut *out, int3
     if (threadIdx.x == 0) {
         out->t_blk = static_cast<long long>(g);
         out->n_act = off;
+        if (LOOP) loop_decide(la, static_cast<long long>(g), off);
     }
 }
 
-// One thread: decides whether the device-side block loop runs another block.
-__global__ void step_loop_kernel(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
-                                 long long n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L)
+// The loop's decision after the multi-block scheduler; one thread.
+__global__ void step_loop_kernel(const SchedOut *next, const LoopArgs la)
 {
-    const long long t = next->t_blk, na = next->n_act;
-    const bool go = L->budget > 0 && (st->flags & stop_flags) == 0u && t <= L->t_end && na > 0 && na < n_fits &&
-                    fits[na] != 0;
-    if (go) {
-        L->budget -= 1;
-        L->blocks += 1;
-        L->rows += na;
-        L->last_t = t;
-    }
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    loop_decide(la, next->t_blk, next->n_act);
 }
 
 // ------------------------------------------------------------------ energy
@@ -408,8 +416,10 @@ cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
                            cudaStream_t s, int64_t *launches, const long long *t_dev)
 {
-    predict_kernel<<<blocks_for(S.n, kThreads, 152 * 64), kThreads, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
-                                                                           lo_parts, t_dev);
+    // FP64 per particle: small n spread over more SMs (GB300's FP64 rate per SM is low)
+    const int tpb = S.n >= 152 * 128 ? kThreads : 32;
+    predict_kernel<<<blocks_for(S.n, tpb, 152 * 64 * (kThreads / tpb)), tpb, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
+                                                                                   lo_parts, t_dev);
     ++*launches;
     return cudaGetLastError();
 }
@@ -446,7 +456,7 @@ cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut 
 {
     const SchedGeom g = sched_geom(S.n);
     if (g.blocks == 1) {
-        sched_single_kernel<<<1, kSchedSingleThreads, 0, s>>>(S, lmax, out, active);
+        sched_single_kernel<false><<<1, kSchedSingleThreads, 0, s>>>(S, lmax, out, active, LoopArgs{});
         ++*launches;
         return cudaGetLastError();
     }
@@ -459,11 +469,17 @@ cudaError_t schedule_launch(const State &S, int lmax, int32_t *active, SchedOut 
     return cudaGetLastError();
 }
 
-cudaError_t step_loop_launch(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
-                             int64_t n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L,
-                             cudaStream_t s, int64_t *launches)
+cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, SchedOut *out, void *scratch,
+                                 const LoopArgs &la, cudaStream_t s, int64_t *launches)
 {
-    step_loop_kernel<<<1, 1, 0, s>>>(h, next, fits, n_fits, st, stop_flags, L);
+    if (sched_geom(S.n).blocks == 1) {
+        sched_single_kernel<true><<<1, kSchedSingleThreads, 0, s>>>(S, lmax, out, active, la);
+        ++*launches;
+        return cudaGetLastError();
+    }
+    cudaError_t e = schedule_launch(S, lmax, active, out, scratch, s, launches);
+    if (e != cudaSuccess) return e;
+    step_loop_kernel<<<1, 1, 0, s>>>(out, la);
     ++*launches;
     return cudaGetLastError();
 }

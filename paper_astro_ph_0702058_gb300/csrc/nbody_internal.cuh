@@ -146,12 +146,22 @@ struct StepLoop {
     long long rows;    // their active rows
     long long last_t;  // block time of the last block that ran
 };
-// Last node of the loop body: the next block (scheduled in `next`) runs when
-// no flag of stop_flags is raised in st, it is due by t_end, its size na has
-// 0 < na < n_fits and fits[na] != 0, and budget is left; sets the condition.
-cudaError_t step_loop_launch(cudaGraphConditionalHandle h, const SchedOut *next, const unsigned char *fits,
-                             int64_t n_fits, const DevStatus *st, unsigned stop_flags, StepLoop *L,
-                             cudaStream_t s, int64_t *launches);
+// What the loop's decision reads: the next block (scheduled in the same body)
+// runs when no flag of stop_flags is raised in st, it is due by L->t_end, its
+// size na has 0 < na < n_fits and fits[na] != 0, and L->budget is left.
+struct LoopArgs {
+    cudaGraphConditionalHandle h;
+    const unsigned char *fits;
+    long long n_fits;
+    const DevStatus *st;
+    unsigned stop_flags;
+    StepLoop *L;
+};
+// Last nodes of the loop body: the next block's schedule (as schedule_launch)
+// and the loop's decision, which sets the condition of la.h (fused into the
+// scheduler's kernel when it is one block, n <= 2048).
+cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, SchedOut *out, void *scratch,
+                                 const LoopArgs &la, cudaStream_t s, int64_t *launches);
 
 // E_kin and E_pot (phi scratch: n doubles; out: 2 doubles).
 cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, double *out,
