@@ -78,3 +78,32 @@ def test_python_binding_rejects_wrong_dtypes():
         _lib.ptr(np.zeros(3, dtype=np.float32), "f64")
     with pytest.raises(ValueError):
         _lib.ptr(np.zeros((3, 3))[:, 0], "f64")
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program compiled against include/nbody.h."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = [f'printf("%zu\\n", sizeof({struct}));'] + [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"nbody.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["nbody_params", "nbody_stats"])
+def test_binding_structs_match_header_layout(name, tmp_path):
+    """The ctypes mirrors have the header's size and field offsets (the library writes whole structs)."""
+    import ctypes as C
+
+    from paper_astro_ph_0702058_gb300 import _lib
+    cls = getattr(_lib, name)
+    fields = [f for f, _ in cls._fields_]
+    size, offsets = _c_layout(name, fields, tmp_path)
+    assert C.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offsets
