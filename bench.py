@@ -490,7 +490,11 @@ def c1_run(args):
             sim.sync()
             wall = time.perf_counter() - t0
             e1 = sum(sim.energy())
-        rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "energy_error": abs((e1 - e0) / e0)})
+            st = sim.stats()
+        # graph_blocks: blocks run inside step-graph replays; loop_blocks: of those, the ones the
+        # device-side loop ran without a host round trip
+        rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "energy_error": abs((e1 - e0) / e0),
+                     "graph_blocks": int(st["graph_blocks"]), "loop_blocks": int(st["loop_blocks"])})
     # cpu_baseline leg: the FP64 oracle's own run of C1 on the host cores
     oracle.set_threads(len(os.sched_getaffinity(0)))
     st = oracle.State(m, x, v, eps2, 0.01, lmin=6, lmax=26).init()
