@@ -63,3 +63,30 @@ def test_device_loop_honours_max_steps(torch, max_steps):
     assert nb_s == nb_g == max_steps and st_g["blocks"] == max_steps
     for key in s_g:
         assert np.array_equal(s_g[key], s_s[key]), key
+
+
+def test_device_loop_stops_at_the_strict_error_block(torch):
+    """Strict mode: the device loop stops after the block whose criterion fell below dt_min, and the
+    call fails there with the state the host loop leaves."""
+    from paper_astro_ph_0702058_gb300 import NBodyError, Simulation, nbody_debug_step_graphs
+    m, x, v = plummer_sphere(500, 8)
+    n = len(m)
+    res = {}
+    for level in (0, 2):
+        nbody_debug_step_graphs(level)
+        try:
+            with Simulation(m, x, v, EPS2, lmin=6, lmax=8, strict=True) as sim:  # lmax = 8 is far too coarse
+                with pytest.raises(NBodyError) as e:
+                    sim.step(1.0 / 64)
+                assert e.value.code == -4
+                out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), a=np.zeros((n, 3)), k=np.zeros((n, 3)),
+                           t_tick=np.zeros(n, dtype=np.int64), level=np.zeros(n, dtype=np.int8))
+                sim.get_state(**out)
+                res[level] = (sim.stats(), out)
+        finally:
+            nbody_debug_step_graphs(2)
+    (st0, s0), (st2, s2) = res[0], res[2]
+    assert st0["blocks"] == st2["blocks"] and st0["below_dt_min"] == st2["below_dt_min"]
+    assert st0["graph_blocks"] == 0 and st2["graph_blocks"] == st2["blocks"]
+    for key in s0:
+        assert np.array_equal(s0[key], s2[key]), key
