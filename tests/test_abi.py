@@ -107,3 +107,35 @@ def test_binding_structs_match_header_layout(name, tmp_path):
     size, offsets = _c_layout(name, fields, tmp_path)
     assert C.sizeof(cls) == size
     assert [getattr(cls, f).offset for f in fields] == offsets
+
+
+def test_every_call_rejects_a_null_handle_without_gpu(libpath):
+    """Each call that takes a context or ensemble checks its pointers before any device work: with null
+    arguments it returns EINVAL (no crash, no CUDA call), on a machine without a GPU."""
+    import ctypes as C
+
+    from paper_astro_ph_0702058_gb300 import _lib
+    L = _lib.lib()
+
+    def null_args(fn):
+        out = []
+        for t in fn.argtypes:
+            if t in (C.c_int, C.c_int64):
+                out.append(1)
+            elif t is C.c_double:
+                out.append(0.5)
+            else:
+                out.append(None)
+        return out
+
+    names = ["nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct", "nbody_step", "nbody_sync",
+             "nbody_energy", "nbody_get_state", "nbody_set_state", "nbody_get_predicted", "nbody_get_stats",
+             "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
+             "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_diff_rollout",
+             "nbody_force_noalloc"]
+    for name in names:
+        fn = getattr(L, name)
+        assert fn(*null_args(fn)) == _lib.NBODY_EINVAL, name
+        assert _lib.nbody_last_error(), name
+    L.nbody_ens_free(None)
+    L.nbody_free(None)
