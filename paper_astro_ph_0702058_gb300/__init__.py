@@ -23,6 +23,53 @@ from ._lib import (NBODY_MODE_COMP, NBODY_MODE_DS, NBODY_MODE_PLAIN, NBODY_MODE_
 MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP, "sumcheck": NBODY_MODE_SUMCHECK,
          "sorted": NBODY_MODE_SORTED, "ds": NBODY_MODE_DS}
 
+_STATE_KEYS = ("x", "v", "a", "k", "t_tick", "level")
+_PARAM_KEYS = ("eta", "eta_init", "lmin", "lmax", "mode", "strict", "i_block", "j_tile", "j_split")
+
+
+def write_checkpoint(path, m, eps2, params, state) -> None:
+    """Writes an ``.npz`` checkpoint: the masses ``m`` (n,), eps^2, the integrator parameters (a dict of
+    ``Simulation``'s keyword arguments) and the state of ``Simulation.get_state``: x, v, a, k (n, 3)
+    float64, t_tick (n,) int64 ticks of 2^-lmax and level (n,) int8 (dt = 2^-level)."""
+    import json
+
+    import numpy as np
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    n = m.shape[0]
+    want = {"x": (np.float64, (n, 3)), "v": (np.float64, (n, 3)), "a": (np.float64, (n, 3)),
+            "k": (np.float64, (n, 3)), "t_tick": (np.int64, (n,)), "level": (np.int8, (n,))}
+    out = {}
+    for key, (dt, shape) in want.items():
+        a = np.asarray(state[key])
+        if a.dtype != dt or a.shape != shape:
+            raise ValueError(f"checkpoint field {key}: need {np.dtype(dt).name} {shape}, got {a.dtype} {a.shape}")
+        out[key] = a
+    unknown = set(params) - set(_PARAM_KEYS)
+    if unknown:
+        raise ValueError(f"unknown parameters {sorted(unknown)}")
+    np.savez(path, m=m, eps2=np.float64(eps2), params=np.array(json.dumps(params, sort_keys=True)), **out)
+
+
+def read_checkpoint(path):
+    """(m, eps2, params, state) from a file of ``write_checkpoint``; no pickled objects are read."""
+    import json
+
+    import numpy as np
+    with np.load(path, allow_pickle=False) as d:
+        m = np.ascontiguousarray(d["m"], dtype=np.float64)
+        eps2 = float(d["eps2"])
+        params = json.loads(str(d["params"]))
+        state = {key: np.ascontiguousarray(d[key]) for key in _STATE_KEYS}
+    n = m.shape[0]
+    for key in ("x", "v", "a", "k"):
+        if state[key].dtype != np.float64 or state[key].shape != (n, 3):
+            raise ValueError(f"checkpoint field {key} has {state[key].dtype} {state[key].shape}")
+    if state["t_tick"].dtype != np.int64 or state["t_tick"].shape != (n,):
+        raise ValueError("checkpoint field t_tick must be int64 (n,)")
+    if state["level"].dtype != np.int8 or state["level"].shape != (n,):
+        raise ValueError("checkpoint field level must be int8 (n,)")
+    return m, eps2, params, state
+
 
 class Simulation:
     """One library context: masses, FP64 state and j-stream on the current CUDA device.
@@ -47,6 +94,10 @@ class Simulation:
         self.lmin, self.lmax = p.lmin, p.lmax
         self.mode = p.mode
         self.stream = stream
+        self.eps2 = float(eps2)
+        self._m = m.detach().clone() if hasattr(m, "detach") else m.copy()  # fixed masses, for checkpoints
+        self._params = {"eta": p.eta, "eta_init": p.eta_init, "lmin": p.lmin, "lmax": p.lmax, "mode": p.mode,
+                        "strict": bool(p.strict), "i_block": p.i_block, "j_tile": p.j_tile, "j_split": p.j_split}
         self._ctx = nbody_init(self.n, m, x, v, eps2, p)
 
     @property
@@ -84,6 +135,28 @@ class Simulation:
 
     def set_state(self, x, v, a, k, t_tick, level):
         nbody_set_state(self.handle, self.n, x, v, a, k, t_tick, level)
+
+    def checkpoint(self, path):
+        """Writes masses, eps^2, parameters and the FP64 state to an ``.npz`` file (``write_checkpoint``);
+        ``Simulation.from_checkpoint`` resumes from it bit for bit."""
+        import numpy as np
+        n = self.n
+        st = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), a=np.zeros((n, 3)), k=np.zeros((n, 3)),
+                  t_tick=np.zeros(n, dtype=np.int64), level=np.zeros(n, dtype=np.int8))
+        self.get_state(**st)
+        m = self._m.detach().cpu().numpy() if hasattr(self._m, "detach") else self._m
+        write_checkpoint(path, m, self.eps2, self._params, st)
+
+    @classmethod
+    def from_checkpoint(cls, path, stream=None):
+        """A new context holding the state of ``path`` (see ``checkpoint``)."""
+        m, eps2, params, st = read_checkpoint(path)
+        params = dict(params)
+        if params.get("eta_init", 0.0) <= 0.0:
+            params["eta_init"] = None
+        sim = cls(m, st["x"], st["v"], eps2, stream=stream, **params)
+        sim.set_state(**st)
+        return sim
 
     def get_predicted(self, posm=None, vel=None, poslo=None):
         nbody_get_predicted(self.handle, self.n, posm, vel, poslo)

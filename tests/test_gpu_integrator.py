@@ -231,6 +231,25 @@ def test_checkpoint_resume_is_bit_exact(torch):
         assert np.array_equal(end_a[key], end_b[key]), key
 
 
+def test_checkpoint_file_resume_is_bit_exact(torch, tmp_path):
+    """Simulation.checkpoint writes an .npz file; a new context from it continues bit for bit."""
+    from paper_astro_ph_0702058_gb300 import Simulation
+    n = 2000
+    m, x, v = plummer_sphere(n, 6)
+    path = tmp_path / "mid.npz"
+    with _sim(m, x, v, mode="comp") as a:
+        a.step(1.0 / 64)
+        a.checkpoint(path)
+        a.step(2.0 / 64)
+        end_a = _get_state(a)
+    with Simulation.from_checkpoint(path) as b:
+        assert b.mode == a.mode and (b.lmin, b.lmax) == (a.lmin, a.lmax) and b.eps2 == a.eps2
+        b.step(2.0 / 64)
+        end_b = _get_state(b)
+    for key in end_a:
+        assert np.array_equal(end_a[key], end_b[key]), key
+
+
 def test_step_reaches_end_time_and_counts(torch):
     n = 4096
     m, x, v = plummer_sphere(n, 7)
