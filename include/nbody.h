@@ -252,8 +252,9 @@ void nbody_debug_skip_tile_copy(int on);
  *   2  (default) the block step is the body of a device-side loop (a while-node
  *      of the graph): after each block's schedule one thread lets the next
  *      block run in the same replay while it is due by t_end, takes the
- *      graph's launch shape, no error flag is raised and at most 1024 blocks
- *      have run; the host then reads back the next block.  Without while-nodes
+ *      graph's launch shape, no error flag is raised and the loop has added
+ *      fewer than 1024 blocks to the replay's first; the host then reads back
+ *      the next block.  Without while-nodes
  *      it acts as 1.
  * A context captures its graph in the form of the level in force when it
  * builds it (once, and again only if its scratch buffer moves); a loop graph

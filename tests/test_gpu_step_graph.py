@@ -32,7 +32,7 @@ def _run(m, x, v, mode, t_end, eta, graphs, max_steps=0):
 
 
 @pytest.mark.parametrize("mode", ["plain", "comp"])
-# (1024, 1.0, 0.01) runs ~3000 blocks: replays of the device loop end at its cap of 1024 blocks
+# (1024, 1.0, 0.01) runs ~5000 blocks: replays of the device loop end at its cap (1 + 1024 blocks)
 @pytest.mark.parametrize("n,t_end,eta", [(1024, 0.125, 0.01), (1024, 1.0, 0.01), (4099, 1.0 / 64, 0.02),
                                          (65536, 1.0 / 64, 0.02)])
 def test_graph_blocks_equal_separate_launches(torch, mode, n, t_end, eta):
