@@ -350,26 +350,28 @@ void nbody_ens_free(nbody_ens *e);
  * while they run (a host application that owns all GPU memory through its
  * own pool, code under a latency budget that cannot afford an allocation or
  * the synchronisation of a free, deployments whose footprint must be fixed
- * at load time).  It evaluates the same sums as nbody_force (Eq. Force with
- * the Appendix A pair term, j = i excluded), always with the j-range split
- * and its partial sums held in a fixed scratch array inside the library:
- * 16 MiB of device memory that every GPU loading the library holds until the
- * process exits.
+ * at load time).  It evaluates the same sums as nbody_force, with j = i
+ * excluded, always with the j-range split and its partial sums held in a
+ * fixed scratch array inside the library: 16 MiB of device memory that
+ * every GPU loading the library holds until the process exits.
  *   posm, vel (and poslo in NBODY_MODE_COMP): the caller's predicted j-stream,
- *     device memory, n_pad = 256 * ceil(n / 256) entries of 4 floats each, in
- *     the layout nbody_get_predicted returns: (x, y, z, m), (vx, vy, vz, 0),
+ *     16-byte aligned device memory of the current device, n_pad =
+ *     256 * ceil(n / 256) entries of 4 floats each, in the layout
+ *     nbody_get_predicted returns: (x, y, z, m), (vx, vy, vz, 0),
  *     (x_lo, y_lo, z_lo, 0).  Entries n .. n_pad-1 must have zero mass and lie
  *     away from every particle (the library pads with (1e15, 1e15, 1e15, 0)).
- *   active[n_act]: device int32 indices, 0 <= n_act <= 131072 (the scratch
- *     limit; larger blocks return NBODY_EINVAL).
- *   acc, jerk (n_act x 3), pot (n_act): device doubles, written.
+ *   active[n_act]: int32 indices in device memory of the current device,
+ *     0 <= n_act <= 131072 (the scratch limit; larger blocks return
+ *     NBODY_EINVAL).
+ *   acc, jerk (n_act x 3), pot (n_act): 8-byte aligned device doubles of the
+ *     current device, written.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the scratch array: calls that
  * overlap on the GPU race, so serialise them.  The call waits for its work
- * on `stream` and returns NBODY_EINVAL (bad argument, host pointer, index out
- * of range), NBODY_ETIMEOUT or NBODY_ECUDA; it never calls cudaMalloc,
- * cudaFree or any allocating routine. */
+ * on `stream` and returns NBODY_EINVAL (bad argument; a host, misaligned or
+ * other-device pointer; index out of range), NBODY_ETIMEOUT or NBODY_ECUDA;
+ * it never calls cudaMalloc, cudaFree or any allocating routine. */
 int nbody_force_noalloc(const float *posm, const float *vel, const float *poslo, int64_t n,
                         const int32_t *active, int64_t n_act, double eps2, int mode,
                         double *acc, double *jerk, double *pot, void *stream);

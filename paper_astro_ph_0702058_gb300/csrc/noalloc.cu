@@ -19,7 +19,10 @@
 // by the caller.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "nbody_internal.cuh"
 
@@ -36,13 +39,17 @@ static __device__ __align__(256) float g_noalloc_partials[kNoAllocPartialFloats]
 static __device__ __align__(256) DevStatus g_noalloc_status;
 
 // Device addresses of the two arrays, looked up once per device (host code
-// only sees a host-side stand-in for a __device__ variable's name).
+// only sees a host-side stand-in for a __device__ variable's name).  The
+// look-up runs under g_setup_lock; `ready` is published with release order
+// after the addresses are written, so a thread that reads it as true with
+// acquire order also sees the addresses.
 struct SymbolAddrs {
-    bool ready;
+    std::atomic<bool> ready;
     float *partials;
     DevStatus *status;
 };
 SymbolAddrs g_addrs[kMaxDevices];
+std::mutex g_setup_lock;
 
 int fail(int code, const char *msg) { return report_error(code, msg); }
 
@@ -54,14 +61,32 @@ int cuda_fail(cudaError_t e, const char *what)
     return report_error(NBODY_ECUDA, buf);
 }
 
-bool on_device(const void *p)
+bool aligned(const void *p, uintptr_t align) { return reinterpret_cast<uintptr_t>(p) % align == 0; }
+
+// True when p is device memory of device `dev` (or managed memory).
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// Looks up the scratch arrays' device addresses for `dev` (current) once.
+int setup_device(int dev, SymbolAddrs &A)
+{
+    if (A.ready.load(std::memory_order_acquire)) return NBODY_OK;
+    std::lock_guard<std::mutex> g(g_setup_lock);
+    if (A.ready.load(std::memory_order_relaxed)) return NBODY_OK;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&A.partials), g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(partials)");
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&A.status), g_noalloc_status);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+    A.ready.store(true, std::memory_order_release);
+    return NBODY_OK;
 }
 
 }  // namespace
@@ -85,24 +110,29 @@ extern "C" int nbody_force_noalloc(const float *posm, const float *vel, const fl
     if (n_act == 0) return NBODY_OK;
     if (!posm || !vel || !active || !acc || !jerk || !pot || (mode == NBODY_MODE_COMP && !poslo))
         return fail(NBODY_EINVAL, "nbody_force_noalloc: null pointer argument");
-    const void *ptrs[] = {posm, vel, active, acc, jerk, pot};
-    for (const void *q : ptrs)
-        if (!on_device(q)) return fail(NBODY_EINVAL, "nbody_force_noalloc: every buffer must be device memory");
-    if (mode == NBODY_MODE_COMP && !on_device(poslo))
-        return fail(NBODY_EINVAL, "nbody_force_noalloc: every buffer must be device memory");
+
+    // The kernels copy j-tiles with bulk asynchronous copies (16-byte aligned
+    // sources) and load float4, double and int32 values: a misaligned pointer
+    // is rejected here, before any CUDA call, instead of faulting there.
+    const void *jstream[] = {posm, vel, mode == NBODY_MODE_COMP ? poslo : posm};
+    const void *outs[] = {acc, jerk, pot};
+    for (const void *q : jstream)
+        if (!aligned(q, 16)) return fail(NBODY_EINVAL, "nbody_force_noalloc: posm, vel and poslo must be 16-byte aligned");
+    for (const void *q : outs)
+        if (!aligned(q, 8)) return fail(NBODY_EINVAL, "nbody_force_noalloc: acc, jerk and pot must be 8-byte aligned");
+    if (!aligned(active, 4)) return fail(NBODY_EINVAL, "nbody_force_noalloc: active must be 4-byte aligned");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(NBODY_EINVAL, "nbody_force_noalloc: device ordinal too large");
+    const void *all[] = {posm, vel, mode == NBODY_MODE_COMP ? poslo : posm, acc, jerk, pot, active};
+    for (const void *q : all)
+        if (!on_device(q, dev))
+            return fail(NBODY_EINVAL, "nbody_force_noalloc: every buffer must be device memory of the current device");
     SymbolAddrs &A = g_addrs[dev];
-    if (!A.ready) {  // set-up on the first call on this device (with it current)
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&A.partials), g_noalloc_partials);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(partials)");
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&A.status), g_noalloc_status);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
-        A.ready = true;
-    }
+    const int rs = setup_device(dev, A);  // first call on this device (with it current)
+    if (rs != NBODY_OK) return rs;
     int sm_count = 0;
     e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "SM count");

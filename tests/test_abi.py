@@ -139,3 +139,28 @@ def test_every_call_rejects_a_null_handle_without_gpu(libpath):
         assert _lib.nbody_last_error(), name
     L.nbody_ens_free(None)
     L.nbody_free(None)
+
+
+def test_noalloc_rejects_misaligned_pointers_without_gpu(libpath):
+    """nbody_force_noalloc checks the alignment its kernels need (16 bytes for the j-stream, which
+    bulk asynchronous copies read; 8 for the outputs; 4 for the list) before any CUDA call, so a
+    misaligned pointer returns EINVAL instead of reaching a kernel.  The addresses below are
+    never dereferenced: the call returns before it touches memory."""
+    import ctypes as C
+
+    from paper_astro_ph_0702058_gb300 import _lib
+    L = _lib.lib()
+    good16, good8, good4 = 0x10000, 0x20000, 0x30000
+    plain = _lib.NBODY_MODE_PLAIN
+
+    def call(posm=good16, vel=good16, poslo=good16, act=good4, acc=good8, jerk=good8, pot=good8, mode=plain):
+        return L.nbody_force_noalloc(C.c_void_p(posm), C.c_void_p(vel), C.c_void_p(poslo), 1000, C.c_void_p(act),
+                                     10, C.c_double(1e-4), mode, C.c_void_p(acc), C.c_void_p(jerk),
+                                     C.c_void_p(pot), None)
+
+    for kw, what in ((dict(posm=good16 + 8), "16-byte"), (dict(vel=good16 + 4), "16-byte"),
+                     (dict(poslo=good16 + 8, mode=_lib.NBODY_MODE_COMP), "16-byte"),
+                     (dict(acc=good8 + 4), "8-byte"), (dict(pot=good8 + 2), "8-byte"),
+                     (dict(act=good4 + 2), "4-byte")):
+        assert call(**kw) == _lib.NBODY_EINVAL, kw
+        assert what in _lib.nbody_last_error(), (kw, _lib.nbody_last_error())

@@ -61,6 +61,37 @@ def test_noalloc_matches_nbody_force_twice(mode):
             check_force(mode, m, x, v, EPS2, act, got, oracle.force(m, x, v, EPS2, act), f"no-alloc call {call}")
 
 
+@pytest.mark.parametrize("mode,n,n_act,rows", [
+    ("plain", 200, 77, None),          # one j-tile: no split, the scratch array is not used
+    ("comp", 200, 200, None),
+    ("comp", 262000, 131072, 512),     # the largest block: the split is capped to the two ranges that fit
+])
+def test_noalloc_single_tile_and_scratch_limit(mode, n, n_act, rows):
+    """The two edges of the split rule: a single j-tile (split 1) and a block of 131072 rows, where
+    only two j-ranges of partial sums fit the scratch array.  Each is compared with nbody_force on the
+    same j-stream within the per-row FP32 bound, on every row or on a seeded sample of them."""
+    torch = need_gpu()
+    from paper_astro_ph_0702058_gb300 import MODES, Simulation, nbody_force_noalloc
+    m, x, v = plummer_sphere(n, 33)
+    act = active_subset(n, n_act, 4)
+    with Simulation(m, x, v, EPS2, mode=mode) as sim:
+        sim.predict(0.0)
+        posm, vel, lo = _padded_stream(torch, sim, n)
+        ref = gpu_force(sim, act)
+        out = [torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
+               for shape in ((n_act, 3), (n_act, 3), (n_act,))]
+        for call in range(2):
+            nbody_force_noalloc(posm, vel, lo, n, torch.from_numpy(act).cuda(), n_act, EPS2, MODES[mode], *out)
+            got = tuple(t.cpu().numpy() for t in out)
+            assert all(np.isfinite(g).all() for g in got), f"call {call}: rows left unwritten"
+            pick = np.arange(n_act) if rows is None else np.sort(np.random.default_rng(5).choice(n_act, rows, False))
+            B, _ = bounds(m, x, v, EPS2, act[pick], mode)
+            diff = np.stack([np.linalg.norm(got[0][pick] - ref[0][pick], axis=1),
+                             np.linalg.norm(got[1][pick] - ref[1][pick], axis=1),
+                             np.abs(got[2][pick] - ref[2][pick])], axis=1)
+            assert np.all(diff <= B), f"{mode} n={n} call {call}: differs from nbody_force beyond the FP32 bound"
+
+
 def test_noalloc_rejects_blocks_beyond_its_scratch():
     torch = need_gpu()
     from paper_astro_ph_0702058_gb300 import NBODY_MODE_PLAIN, NBodyError, nbody_force_noalloc
