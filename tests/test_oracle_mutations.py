@@ -34,6 +34,9 @@ MUTANTS = {
     "schedule_tie": ("if (tn == tmin) active[na++]", "if (tn <= tmin + 1) active[na++]"),
     "energy_half": ("ep += 0.5 * m[i] * phi[i];", "ep += m[i] * phi[i];"),
     "self_term": ("if (j == i) continue;\n            double dx[3]", "double dx[3]"),
+    # the start of a run: Eq. (initTimestep) wired into the first levels
+    "init_level_off_by_one": ("level[i] = (int8_t)L;", "level[i] = (int8_t)(L + 1);"),
+    "init_other_row_jerk": ("orc_dt_initial(a + 3 * i, k + 3 * i, eta_init)", "orc_dt_initial(a + 3 * i, k, eta_init)"),
     # the summation-check and sorted-summation oracles
     "rsqrt_cmp_flip": ("return P < one ? -1 : (P > one ? 1 : 0);", "return P < one ? 1 : (P > one ? -1 : 0);"),
     "rsqrt_exp_off": ("const int K = 2 * (e0 - 1) + er;", "const int K = 2 * e0 + er;"),
@@ -95,5 +98,34 @@ def test_adjoint_pins_catch_mutant(tmp_path, name):
             "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
             % (ROOT, str(mod), os.path.join(ROOT, "tests", "test_oracle_adjoint.py")))
     r = subprocess.run([sys.executable, "-c", boot], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode not in (0, 4, 5), r.stdout[-2000:] + r.stderr[-2000:]
+    assert "failed" in r.stdout, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+PKG_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+PKG_MUTANTS = {
+    # the wrapper hands eta to the start of a run where eta_init belongs
+    "init_eta_for_eta_init": ("self.n, m, x, v, self.eps2, self.eta_init, self.lmin",
+                              "self.n, m, x, v, self.eps2, self.eta, self.lmin"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PKG_MUTANTS))
+def test_wrapper_pins_catch_mutant(tmp_path, name):
+    """The same for the oracle's Python wrapper: a copy of the oracle package with one mistake in
+    __init__.py (its C source unchanged) is imported in place of the real one before the pins run."""
+    old, new = PKG_MUTANTS[name]
+    src = open(PKG_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor missing or ambiguous: {old!r}"
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    for f in ("oracle.c", "oracle.h", "adjoint.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), pkg / f)
+    (pkg / "__init__.py").write_text(src.replace(old, new, 1))
+    boot = ("import sys; sys.path.insert(0, %r); import oracle; assert oracle.__file__.startswith(%r); "
+            "sys.path.insert(1, %r); import pytest; "
+            "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))"
+            % (str(tmp_path), str(tmp_path), ROOT, os.path.join(ROOT, "tests", "test_oracle_pins.py")))
+    r = subprocess.run([sys.executable, "-c", boot], cwd=str(tmp_path), capture_output=True, text=True, timeout=600)
     assert r.returncode not in (0, 4, 5), r.stdout[-2000:] + r.stderr[-2000:]
     assert "failed" in r.stdout, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -249,6 +249,39 @@ def test_aarseth_criterion_circular_orbit_closed_form(orc):
     assert abs(orc.dt_initial(a, k, eta) - eta / w) < 1e-16
 
 
+def test_init_levels_circular_binaries_closed_form(orc):
+    """Eq. (initTimestep) through the oracle's start of a run.  For a circular binary of total mass 1 and
+    separation d (eps = 0) each body has |a| = 1/(2 d^2) and, since dx.dv = 0, |k| = |dv|/(2 d^3) with
+    |dv| = d^(-1/2); so |a|/|k| = d^(3/2) exactly and the first step is the largest power of two not above
+    eta_init d^(3/2).  Two binaries 10^6 apart (cross terms ~1e-12 relative) with different d must get the
+    levels worked out by hand below; eta is set apart from eta_init, so taking one for the other, an
+    off-by-one level or another particle's force changes them."""
+    # (d, eta_init, level): eta_init d^1.5 and the bin [2^-L, 2^-(L-1)) it falls in
+    cases = [
+        (1.0, 0.01, 7),      # 0.01     in [0.0078125, 0.015625)
+        (0.25, 0.01, 10),    # 0.00125  in [0.0009765625, 0.001953125)
+        (4.0, 0.003, 6),     # 0.024    in [0.015625, 0.03125)
+        (0.25, 0.003, 12),   # 0.000375 in [0.000244140625, 0.00048828125)
+    ]
+    for (d1, eta_init, l1), (d2, eta_init2, l2) in zip(cases[::2], cases[1::2]):
+        assert eta_init == eta_init2
+        for d, lv in ((d1, l1), (d2, l2)):
+            dt = eta_init * d ** 1.5
+            assert 2.0 ** -lv <= dt * (1 - 1e-6) and dt * (1 + 1e-6) < 2.0 ** (1 - lv)
+        ma, xa, va = kepler_pair(0.0, a=d1)
+        mb, xb, vb = kepler_pair(0.0, a=d2)
+        m = np.concatenate([ma, mb])
+        x = np.concatenate([xa, xb + np.array([1e6, 0.0, 0.0])])
+        v = np.concatenate([va, vb])
+        st = orc.State(m, x, v, 0.0, 0.05, eta_init=eta_init, lmin=3, lmax=26).init()
+        assert list(st.level) == [l1, l1, l2, l2], (d1, d2, eta_init, list(st.level))
+        assert np.all(st.t == 0)
+        # the forces it stored are the binaries' own, to the 1e-12 of the far pair
+        for i, d in enumerate((d1, d1, d2, d2)):
+            assert abs(np.linalg.norm(st.a[i]) * 2 * d * d - 1) < 1e-10
+            assert abs(np.linalg.norm(st.k[i]) * 2 * d ** 3.5 - 1) < 1e-10
+
+
 def test_level_quantisation_edges(orc):
     lmin, lmax = 6, 26
     assert orc.level_floor(2.0 ** -7, lmin, lmax) == (7, False)
