@@ -65,11 +65,12 @@ enum {
     NBODY_MODE_PLAIN = 0,  /* FP32 pair math on FP32 positions, FP32 accumulation           */
     NBODY_MODE_COMP = 1,   /* FP32 pair math on x_j - x_i formed from hi/lo splits of the
                               FP64 positions; double-single (compensated) accumulation      */
-    NBODY_MODE_SUMCHECK = 2, /* test mode for the compensated summation: the pair term of
-                              NBODY_MODE_COMP with the correctly rounded reciprocal square
-                              root and no contracted operations, so that every FP32 term is
-                              reproducible on a CPU, and every term folded into the
-                              double-single sums on its own (the production mode sums 64
+    NBODY_MODE_SUMCHECK = 2, /* test mode for the compensated summation: the production
+                              kernel's tiles, j-ranges and packed pair loop with the pair term
+                              of NBODY_MODE_COMP formed with the correctly rounded reciprocal
+                              square root and no contracted operations, so that every FP32 term
+                              is reproducible on a CPU, and every term folded into the
+                              double-single sums on its own (the production mode sums 128
                               terms in FP32 first).  Slower; nbody_force / nbody_step only
                               (not the ensemble or the no-alloc entry point).              */
     NBODY_MODE_SORTED = 3, /* ablation of the accumulation order (Sect. 6 of the paper): the

@@ -1,7 +1,7 @@
 // Launch and dispatch of the force kernels over the compiled launch shapes.
-// The plain and compensated modes run the packed-FP32 pair loop
-// (force_x2.cuh); building with -DNB_PACKED=0 selects the scalar loop of
-// force_impl.cuh instead.  The summation-check mode always runs the scalar loop.
+// The plain, compensated and summation-check modes run the packed-FP32 pair
+// loop (force_x2.cuh); building with -DNB_PACKED=0 selects the scalar loop of
+// force_impl.cuh instead.
 #pragma once
 
 #include "force_impl.cuh"
@@ -24,7 +24,7 @@ cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, 
 {
     dim3 grid(cfg.n_iblk, cfg.split);
     constexpr int PF = FoldLen<MODE>::value;
-    if constexpr (NB_PACKED && MODE != kModeCheck) {
+    if constexpr (NB_PACKED) {
         if (P.soa) {
             force_kernel_x2<MODE, NT, IPT, PF, true><<<grid, NT, 0, s>>>(P);
             return cudaGetLastError();
@@ -41,7 +41,7 @@ cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, 
 template <int MODE, int NT, int IPT>
 int occupancy_instance(int *blocks)
 {
-    if constexpr (NB_PACKED && MODE != kModeCheck)
+    if constexpr (NB_PACKED)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             blocks, force_kernel_x2<MODE, NT, IPT, FoldLen<MODE>::value, true>, NT, 0);
     else

@@ -129,12 +129,94 @@ __device__ __forceinline__ void pair_term_x2(const f2_t X, const f2_t Y, const f
     p[6] = f2_sub(p[6], mr);
 }
 
+// Knuth's TwoSum on both halves at once: hi + x == s + e exactly per half,
+// e kept in lo (fold_ds of force_impl.cuh, packed).  Inline PTX is never
+// contracted, so every operation rounds as written.
+__device__ __forceinline__ void fold_ds_x2(f2_t &hi, f2_t &lo, const f2_t x)
+{
+    const f2_t s = f2_add(hi, x);
+    const f2_t bb = f2_sub(s, hi);
+    const f2_t e = f2_add(f2_sub(hi, f2_sub(s, bb)), f2_sub(x, bb));
+    hi = s;
+    lo = f2_add(lo, e);
+}
+
+// Summation-check form of pair_term_x2 (kModeCheck): the compensated pair term
+// with the correctly rounded reciprocal square root (per half), every term
+// formed by its own product (no multiply-add into the sums), and each of the
+// 7 terms of each half folded at once into packed double-single sums (fold
+// length 1).  The operations and their order are those of the CPU's FP32-term
+// sums, so both form the same FP32 terms:
+//   dx = (xj_hi - xi_hi) + (xj_lo - xi_lo);  dv = vj - vi
+//   r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));  rinv = rsqrt_rn(r2)
+//   xv = fma(dz, dvz, fma(dy, dvy, dx * dvx));  mr = m rinv;  mr3 = mr (rinv rinv)
+//   terms: mr3 dx,  mr3 fma(-3 (xv (rinv rinv)), dx, dv),  -mr
+// (x (-3) rounds to the negation of 3 x, so the jerk term is the CPU's bit for bit.)
+template <bool SELF>
+__device__ __forceinline__ void pair_term_x2_check(const f2_t X, const f2_t Y, const f2_t Z, const f2_t M,
+                                                   const f2_t VX, const f2_t VY, const f2_t VZ, const f2_t LX,
+                                                   const f2_t LY, const f2_t LZ, const I2 &I, const f2_t E2,
+                                                   const f2_t NEG3, const int j_even, const int gi, f2_t (&hi)[7],
+                                                   f2_t (&lo)[7])
+{
+    const f2_t dx = f2_add(f2_sub(X, I.x), f2_sub(LX, I.lx));
+    const f2_t dy = f2_add(f2_sub(Y, I.y), f2_sub(LY, I.ly));
+    const f2_t dz = f2_add(f2_sub(Z, I.z), f2_sub(LZ, I.lz));
+    const f2_t dvx = f2_sub(VX, I.vx), dvy = f2_sub(VY, I.vy), dvz = f2_sub(VZ, I.vz);
+    const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, E2)));
+    float r2a, r2b;
+    f2_unpack(r2, r2a, r2b);
+    float ra = __frsqrt_rn(r2a), rb = __frsqrt_rn(r2b);
+    if (SELF) {  // j = i: every term becomes an exact zero, and folding a zero changes nothing
+        ra = (j_even == gi) ? 0.0f : ra;
+        rb = (j_even + 1 == gi) ? 0.0f : rb;
+    }
+    const f2_t rinv = f2_pack(ra, rb);
+    const f2_t xv = f2_fma(dz, dvz, f2_fma(dy, dvy, f2_mul(dx, dvx)));
+    const f2_t rinv2 = f2_mul(rinv, rinv);
+    const f2_t mr = f2_mul(M, rinv);
+    const f2_t mr3 = f2_mul(mr, rinv2);
+    const f2_t wn = f2_mul(f2_mul(xv, rinv2), NEG3);
+    fold_ds_x2(hi[0], lo[0], f2_mul(mr3, dx));
+    fold_ds_x2(hi[1], lo[1], f2_mul(mr3, dy));
+    fold_ds_x2(hi[2], lo[2], f2_mul(mr3, dz));
+    fold_ds_x2(hi[3], lo[3], f2_mul(mr3, f2_fma(wn, dx, dvx)));
+    fold_ds_x2(hi[4], lo[4], f2_mul(mr3, f2_fma(wn, dy, dvy)));
+    fold_ds_x2(hi[5], lo[5], f2_mul(mr3, f2_fma(wn, dz, dvz)));
+    fold_ds_x2(hi[6], lo[6], f2_sub(0ull, mr));
+}
+
 // Structure-of-arrays copy of one tile: x y z m vx vy vz (lx ly lz).
 template <int MODE>
 struct SoaTile {
-    static constexpr int NA = (MODE == kModeComp) ? 10 : 7;
+    static constexpr int NA = is_ds(MODE) ? 10 : 7;
     float a[NA][kJTile];
 };
+
+// Summation-check sums over one tile: every pair term of each half folded
+// into the packed double-single sums ph, pl.
+template <int IPT, bool SELF>
+__device__ __forceinline__ void tile_sums_x2_check(const SoaTile<kModeCheck> &T, const int j0, const I2 (&I)[IPT],
+                                                   const int (&gi)[IPT], const f2_t E2, const f2_t NEG3,
+                                                   f2_t (&ph)[IPT][7], f2_t (&pl)[IPT][7])
+{
+#pragma unroll 2
+    for (int jj = 0; jj < kJTile; jj += 4) {
+        f2_t v[10][2];
+#pragma unroll
+        for (int a = 0; a < 10; ++a) {
+            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&T.a[a][jj]);
+            v[a][0] = q.x;
+            v[a][1] = q.y;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+                pair_term_x2_check<SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h], v[7][h],
+                                         v[8][h], v[9][h], I[u], E2, NEG3, j0 + jj + 2 * h, gi[u], ph[u], pl[u]);
+    }
+}
 
 template <int MODE, int IPT, int PF, bool SELF>
 __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j0, const I2 (&I)[IPT],
@@ -168,9 +250,9 @@ NB_UNROLL(NB_X2_UNROLL)
 #pragma unroll
                 for (int u = 0; u < IPT; ++u)
                     pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
-                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 3][h] : 0ull,
-                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 2][h] : 0ull,
-                                             MODE == kModeComp ? v[SoaTile<MODE>::NA - 1][h] : 0ull, I[u], E2,
+                                             is_ds(MODE) ? v[SoaTile<MODE>::NA - 3][h] : 0ull,
+                                             is_ds(MODE) ? v[SoaTile<MODE>::NA - 2][h] : 0ull,
+                                             is_ds(MODE) ? v[SoaTile<MODE>::NA - 1][h] : 0ull, I[u], E2,
                                              NEG3, j0 + jb + jj + 2 * h, gi[u], p[u]);
         }
 #pragma unroll
@@ -200,11 +282,11 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     // SOAIN: the tiles come straight from the SoA j-stream into the SoA tile
     // buffers (one bulk copy per array, one barrier per tile); otherwise the
     // float4 stream is staged and transposed (two barriers per tile).
-    constexpr int NARR = (MODE == kModeComp) ? 3 : 2;
+    constexpr int NARR = is_ds(MODE) ? 3 : 2;
     constexpr int NA = SoaTile<MODE>::NA;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
     constexpr uint32_t kArrBytes = kJTile * sizeof(float);
-    static_assert(kJTile % PF == 0 && PF % 4 == 0, "fold length");
+    static_assert(MODE == kModeCheck || (kJTile % PF == 0 && PF % 4 == 0), "fold length");
     __shared__ __align__(128) float4 sj[SOAIN ? 1 : 2][SOAIN ? 1 : NARR][SOAIN ? 1 : kJTile];
     // small blocks keep one tile per group: their occupancy is set by shared memory
     constexpr int TG = (SOAIN && NT >= 128) ? NB_X2_TGROUP : 1;
@@ -243,7 +325,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         I[u].vx = f2_pack(vp.x, vp.x);
         I[u].vy = f2_pack(vp.y, vp.y);
         I[u].vz = f2_pack(vp.z, vp.z);
-        if (MODE == kModeComp) {
+        if (is_ds(MODE)) {
             const float4 lp = P.poslo[l];
             I[u].lx = f2_pack(lp.x, lp.x);
             I[u].ly = f2_pack(lp.y, lp.y);
@@ -251,12 +333,15 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         }
     }
     float tot[IPT][7], lo[IPT][7];
+    f2_t ph[IPT][7], pl[IPT][7];  // summation check: packed even/odd double-single sums
 #pragma unroll
     for (int u = 0; u < IPT; ++u)
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             tot[u][c] = 0.0f;
             lo[u][c] = 0.0f;
+            ph[u][c] = 0ull;
+            pl[u][c] = 0ull;
         }
 
     if (tid == 0) {
@@ -281,7 +366,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             mbar_arrive_expect_tx(&bar[b], NARR * kTileBytes);
             bulk_g2s(sj[b][0], P.posm + off, kTileBytes, &bar[b]);
             bulk_g2s(sj[b][1], P.vel + off, kTileBytes, &bar[b]);
-            if (MODE == kModeComp) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
+            if (is_ds(MODE)) bulk_g2s(sj[b][NARR - 1], P.poslo + off, kTileBytes, &bar[b]);
         }
     };
 
@@ -303,7 +388,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
                     soa[0].a[4][e] = vv.x;
                     soa[0].a[5][e] = vv.y;
                     soa[0].a[6][e] = vv.z;
-                    if (MODE == kModeComp) {
+                    if (is_ds(MODE)) {
                         const float4 lv = sj[b][NARR - 1][e];
                         soa[0].a[7][e] = lv.x;
                         soa[0].a[8][e] = lv.y;
@@ -329,10 +414,16 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 #pragma unroll
             for (int u = 0; u < IPT; ++u)
                 self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
-            if (self_tile)
+            if constexpr (MODE == kModeCheck) {
+                if (self_tile)
+                    tile_sums_x2_check<IPT, true>(T, j0, I, gi, E2, NEG3, ph, pl);
+                else
+                    tile_sums_x2_check<IPT, false>(T, j0, I, gi, E2, NEG3, ph, pl);
+            } else if (self_tile) {
                 tile_sums_x2<MODE, IPT, PF, true>(T, j0, I, gi, E2, NEG3, tot, lo);
-            else
+            } else {
                 tile_sums_x2<MODE, IPT, PF, false>(T, j0, I, gi, E2, NEG3, tot, lo);
+            }
         }
         if constexpr (SOAIN) {
             if (__syncthreads_or(!ok)) {
@@ -355,6 +446,21 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         return;
     }
 
+    if constexpr (MODE == kModeCheck) {
+        // even and odd sums into one double-single pair: TwoSum of the high
+        // words, the low words and the error added (all round to nearest)
+#pragma unroll
+        for (int u = 0; u < IPT; ++u)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                float he, ho, le, lo2;
+                f2_unpack(ph[u][c], he, ho);
+                f2_unpack(pl[u][c], le, lo2);
+                tot[u][c] = he;
+                lo[u][c] = __fadd_rn(le, lo2);
+                fold_ds_rn(tot[u][c], lo[u][c], ho);
+            }
+    }
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
         const int q = (blockIdx.x * IPT + u) * NT + tid;
@@ -363,8 +469,8 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             double r[7];
 #pragma unroll
             for (int c = 0; c < 7; ++c)
-                r[c] = (MODE == kModeComp) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
-                                           : static_cast<double>(tot[u][c]);
+                r[c] = is_ds(MODE) ? static_cast<double>(tot[u][c]) + static_cast<double>(lo[u][c])
+                                   : static_cast<double>(tot[u][c]);
             double *pa = P.acc + 3 * static_cast<size_t>(q);
             double *pk = P.jerk + 3 * static_cast<size_t>(q);
             pa[0] = r[0];
@@ -375,12 +481,12 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             pk[2] = r[5];
             P.pot[q] = r[6];
         } else {
-            constexpr int NC = (MODE == kModeComp) ? 14 : 7;
+            constexpr int NC = is_ds(MODE) ? 14 : 7;
             float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * n_act + q;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 base[static_cast<size_t>(c) * n_act] = tot[u][c];
-                if (MODE == kModeComp) base[static_cast<size_t>(7 + c) * n_act] = lo[u][c];
+                if (is_ds(MODE)) base[static_cast<size_t>(7 + c) * n_act] = lo[u][c];
             }
         }
     }

@@ -5,9 +5,11 @@ In the summation-check mode the kernel forms each FP32 pair term of the compensa
 pair term with correctly rounded operations in a fixed order, and folds every term
 into its double-single sums.  The oracle forms the same FP32 terms on the CPU from
 the same FP64 state and adds them exactly; the two must agree to 1e-10 per particle
-(denominators floored at 1e-3 of the rms over the compared rows).  The tiles, the
-j-ranges, the partial layout and the FP64 reduction are those of the compensated
-production kernel."""
+(denominators floored at 1e-3 of the rms over the compared rows).  The kernel is the
+production one (force_kernel_x2): its structure-of-arrays tiles and tile groups, the
+packed two-pair loop with its even and odd j halves, the j-ranges, the partial layout
+and the FP64 reduction are those the compensated benchmark runs; only the pair term's
+rsqrt and the fold length differ."""
 import numpy as np
 import pytest
 
