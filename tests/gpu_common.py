@@ -22,12 +22,12 @@ EPS2 = (1.0 / 256) ** 2
 #    most.  Those rows stay inside their FP32 bound.
 REL = {"plain": 1e-5, "comp": 1e-6}
 FRAC = {  # Plummer spheres with eps = 1/256, N <= 65536
-    "plain": {"acc": 0.99, "acc_mag": 0.99, "pot": 0.99, "jerk": 0.95, "jerk_mag": 0.97},
+    "plain": {"acc": 0.97, "acc_mag": 0.97, "pot": 0.99, "jerk": 0.95, "jerk_mag": 0.97},
     "comp": {"acc": 0.99, "acc_mag": 0.99, "pot": 0.99, "jerk": 0.97, "jerk_mag": 0.99},
 }
 # N = 2^20 with eps = 1e-3: more rows have a close neighbour than at N = 65536
 FRAC_LARGE = {
-    "plain": {"acc": 0.99, "acc_mag": 0.99, "pot": 0.99, "jerk": 0.90, "jerk_mag": 0.95},
+    "plain": {"acc": 0.97, "acc_mag": 0.97, "pot": 0.99, "jerk": 0.90, "jerk_mag": 0.95},
     "comp": FRAC["comp"],
 }
 
