@@ -70,6 +70,16 @@ def sum_over_ranks(value: float, ws: int) -> float:
     return float(t.item())
 
 
+def replica_totals(ws: int, mode_ms: dict, e2e_ms: float, pairs_per_rank: float) -> dict:
+    """Every cross-rank reduction of the benchmark, called by all ranks in one fixed order: per mode
+    and for the end-to-end run, the slowest rank's time and the work of all replicas."""
+    out = {}
+    for mode in sorted(mode_ms):
+        out[mode] = {"t_max": max_over_ranks(mode_ms[mode], ws), "pairs": sum_over_ranks(pairs_per_rank, ws)}
+    out["e2e"] = {"t_max": max_over_ranks(e2e_ms, ws), "pairs": sum_over_ranks(pairs_per_rank, ws)}
+    return out
+
+
 def barrier(ws: int) -> None:
     if ws > 1:
         import torch.distributed as dist
@@ -140,8 +150,9 @@ def make_sim(m, x, v, mode, stream):
     return Simulation(m, x, v, EPS2, eta=0.02, lmin=LEVEL, lmax=LEVEL, mode=mode, stream=stream)
 
 
-def run_steps(sim, n, steps, warmup, stream, flush, host=None):
-    """Times `steps` block steps (after `warmup`).  Returns (total_ms, force_ms_list, launches)."""
+def run_steps(sim, n, steps, warmup, stream, flush, host=None, after_first=None):
+    """Times `steps` block steps (after `warmup`).  Returns (total_ms, force_ms_list, launches).
+    `after_first` (untimed, during the warm-up) is called once after the first step."""
     import torch
     dev_list = torch.zeros(n, dtype=torch.int32, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -171,6 +182,8 @@ def run_steps(sim, n, steps, warmup, stream, flush, host=None):
             sim.correct(lst, n_act)
         e1.record(stream)
         assert n_act == n, n_act
+        if it == 0 and after_first is not None and warmup > 0:
+            after_first()
         if it >= warmup:
             step_ms.append((e0, e1))
             force_ms.append((f0, f1))
@@ -290,20 +303,25 @@ def bench_ours(args):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = measured_peaks()
     res = {}
+    energy = {}
     with torch.cuda.stream(stream):
         for mode in ("comp", "plain"):
             sim = make_sim(m, x, v, mode, stream)
+            if not energy:
+                energy["e0"] = sum(sim.energy(ds_potential=True))  # t = 0: the same state in every mode
+            first = {}
             barrier(ws)
             with ClockSampler(local) as cs:
                 t0 = time.perf_counter()
-                total_ms, force_ms, launches = run_steps(sim, n, args.steps, args.warmup, stream, flush)
+                total_ms, force_ms, launches = run_steps(
+                    sim, n, args.steps, args.warmup, stream, flush,
+                    after_first=lambda: first.setdefault("e", sum(sim.energy(ds_potential=True))))
                 wall = time.perf_counter() - t0
             clocks = cs.summary()
             cfg = sim.stats()
+            energy[mode] = {"end": sum(sim.energy(ds_potential=True)), "first": first.get("e")}
             sim.close()
-            t_max = max_over_ranks(total_ms, ws)
-            pairs_all = sum_over_ranks(args.steps * n * (n - 1), ws)
-            res[mode] = {"value": pairs_all / (t_max * 1e-3), "ms_per_step": t_max / args.steps,
+            res[mode] = {"total_ms": total_ms,
                          "force_ms": statistics.mean(force_ms), "launches": launches, "clocks": clocks,
                          "wall_s": wall, "shape": f"{cfg['last_threads']} threads x {cfg['last_i_per_thread']} "
                                                   f"i/thread, j-split {cfg['last_j_split']}",
@@ -315,13 +333,39 @@ def bench_ours(args):
         barrier(ws)
         e2e_ms, _, _ = run_steps(sim, n, args.steps, args.warmup, stream, flush, host=host)
         sim.close()
-        e2e_max = max_over_ranks(e2e_ms, ws)
+        totals = replica_totals(ws, {mode: r["total_ms"] for mode, r in res.items()}, e2e_ms,
+                                args.steps * n * (n - 1))
+        for mode, r in res.items():
+            t_max = totals[mode]["t_max"]
+            r.update(value=totals[mode]["pairs"] / (t_max * 1e-3), ms_per_step=t_max / args.steps)
+        if rank == 0 and not args.no_energy_reference:
+            # one step in double-single pair arithmetic (~1e-12 from FP64): the FP64 oracle's stand-in,
+            # since the oracle itself would need ~1e12 FP64 pair terms per step on the host
+            with make_sim(m, x, v, "ds", stream) as sim:
+                lst = torch.zeros(n, dtype=torch.int32, device="cuda")
+                t_blk, n_act = sim.next_block(lst)
+                sim.predict(t_blk)
+                sim.force(lst, n_act)
+                sim.correct(lst, n_act)
+                energy["ds"] = {"first": sum(sim.energy(ds_potential=True))}
     out = None
     if rank == 0:
         c = res["comp"]
         p = res["plain"]
         rl_c = roofline(c["force_ms"], n, sm_count, c["clocks"], peaks, "comp", c["launch"])
         rl_p = roofline(p["force_ms"], n, sm_count, p["clocks"], peaks, "plain", p["launch"])
+        e0 = energy["e0"]
+        rel = lambda e: None if e is None else abs((e - e0) / e0)  # noqa: E731
+        steps_all = args.warmup + args.steps
+        energy_info = {
+            "segment": f"this run: {steps_all} full-force Hermite steps of dt = 2^-{LEVEL} from t = 0 "
+                       f"(warm-up and timed), t_end = {steps_all}/{1 << LEVEL}",
+            "diagnostic": "|E(t_end) - E(0)| / |E(0)|; E_kin FP64, E_pot double-single (nbody_energy_ds, "
+                          "~1e-13 relative), outside the timed events",
+            "after_first_step": {"comp": rel(energy["comp"]["first"]), "plain": rel(energy["plain"]["first"]),
+                                 "ds_fp64_standin": rel(energy.get("ds", {}).get("first"))},
+            "fp64_standin": "double-single pair arithmetic (NBODY_MODE_DS, ~1e-12 from the FP64 definition) "
+                            "for the FP64 oracle, which cannot run this size"}
         out = {
             "metric": METRIC, "value": c["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": c["ms_per_step"], "higher_is_better": True,
@@ -335,10 +379,13 @@ def bench_ours(args):
                        f"({L2_FLUSH_BYTES >> 20} MiB write, outside the timed events)",
                        "force_launch_shape": c["shape"], "parallelism": f"replicas x{ws}"},
             "roofline": rl_c,
+            "energy_error": rel(energy["comp"]["end"]),
+            "energy": energy_info,
             "plain": {"value": p["value"], "ms_per_step": p["ms_per_step"], "roofline": rl_p,
+                      "energy_error": rel(energy["plain"]["end"]),
                       "force_launch_shape": p["shape"], "clocks": p["clocks"]},
             "comp_over_plain": c["value"] / p["value"],
-            "e2e": {"value": sum_over_ranks(args.steps * n * (n - 1), ws) / (e2e_max * 1e-3), "unit": UNIT,
+            "e2e": {"value": totals["e2e"]["pairs"] / (totals["e2e"]["t_max"] * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 4 * n, "d2h_bytes_per_step": 4 * n + 7 * 8 * n},
             "gpu_launches": c["launches"],
             "clocks": c["clocks"],
@@ -660,6 +707,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="particles (default 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-energy-reference", action="store_true",
+                    help="skip the one double-single step that stands in for the FP64 oracle's energy error")
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")

@@ -175,6 +175,16 @@ int nbody_step(nbody_ctx *ctx, double t_end, int64_t max_steps, int64_t *n_steps
  * Errors: ENOTSYNC when the particles are not at one time. */
 int nbody_energy(nbody_ctx *ctx, double *ekin, double *epot);
 
+/* The same diagnostic with the potential in double-single arithmetic on the
+ * FP32 pipe: positions, masses and eps2 split into (hi, lo) float pairs,
+ * 1/r from the MUFU seed and one Newton step with a double-single residual,
+ * each 256-particle tile's terms summed in double-single and the tile sums
+ * in FP64.  Agrees with nbody_energy to ~1e-13 relative and avoids an FP64
+ * square root and division per pair, which make nbody_energy take about a
+ * minute at n = 2^20 on GB300.  E_kin is FP64 as in nbody_energy.
+ * Synchronises the stream.  Errors: ENOTSYNC as nbody_energy. */
+int nbody_energy_ds(nbody_ctx *ctx, double *ekin, double *epot);
+
 /* Waits for all work of the context and reports device-side errors raised
  * since the last report: ETIMEOUT (a bounded wait gave up), EINVAL (an index
  * out of range in an active list), ENONFINITE (a non-finite corrected row),

@@ -15,7 +15,7 @@ from ._lib import (NBODY_MODE_COMP, NBODY_MODE_DS, NBODY_MODE_PLAIN, NBODY_MODE_
                    nbody_ens_energy, nbody_ens_free, nbody_ens_get_state, nbody_ens_get_stats,
                    nbody_ens_init, nbody_ens_run, nbody_ens_set_shape, nbody_ens_step, nbody_ens_tune,
                    nbody_correct, nbody_debug_fail_alloc, nbody_debug_skip_tile_copy, nbody_debug_step_graphs,
-                   nbody_default_params, nbody_energy,
+                   nbody_default_params, nbody_energy, nbody_energy_ds,
                    nbody_force, nbody_force_noalloc, nbody_free, nbody_get_predicted, nbody_get_state, nbody_get_stats, nbody_init,
                    nbody_last_error, nbody_next_block, nbody_predict, nbody_set_state, nbody_step,
                    nbody_strerror, nbody_sync)
@@ -127,8 +127,10 @@ class Simulation:
     def sync(self):
         nbody_sync(self.handle)
 
-    def energy(self):
-        return nbody_energy(self.handle)
+    def energy(self, ds_potential=False):
+        """(E_kin, E_pot) at a synchronised time; ``ds_potential`` evaluates the potential in
+        double-single arithmetic (``nbody_energy_ds``: ~1e-13 relative, fast at large N)."""
+        return nbody_energy_ds(self.handle) if ds_potential else nbody_energy(self.handle)
 
     def get_state(self, x=None, v=None, a=None, k=None, t_tick=None, level=None):
         nbody_get_state(self.handle, self.n, x, v, a, k, t_tick, level)

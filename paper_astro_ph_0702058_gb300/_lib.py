@@ -37,7 +37,7 @@ NBODY_MODE_DS = 4
 
 # Every symbol include/nbody.h declares (checked by the tests against the header).
 EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_predict", "nbody_force",
-           "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state",
+           "nbody_correct", "nbody_step", "nbody_sync", "nbody_energy", "nbody_energy_ds", "nbody_get_state",
            "nbody_set_state", "nbody_get_predicted", "nbody_get_stats", "nbody_free", "nbody_strerror", "nbody_last_error",
            "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_debug_step_graphs", "nbody_force_noalloc",
            "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
@@ -89,6 +89,7 @@ def lib():
             L.nbody_step.argtypes = [P, C.c_double, C.c_int64, C.POINTER(C.c_int64)]
             L.nbody_sync.argtypes = [P]
             L.nbody_energy.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.nbody_energy_ds.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.nbody_get_state.argtypes = [P, P, P, P, P, P, P]
             L.nbody_set_state.argtypes = [P, P, P, P, P, P, P]
             L.nbody_get_predicted.argtypes = [P, P, P, P]
@@ -126,7 +127,7 @@ def lib():
                          "nbody_ens_run", "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats"):
                 getattr(L, name).restype = C.c_int
             for name in ("nbody_init", "nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct",
-                         "nbody_step", "nbody_sync", "nbody_energy", "nbody_get_state", "nbody_set_state",
+                         "nbody_step", "nbody_sync", "nbody_energy", "nbody_energy_ds", "nbody_get_state", "nbody_set_state",
                          "nbody_get_predicted", "nbody_get_stats"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -214,6 +215,12 @@ def nbody_sync(ctx) -> None:
 def nbody_energy(ctx):
     ek, ep = C.c_double(), C.c_double()
     _check(lib().nbody_energy(ctx, C.byref(ek), C.byref(ep)), "nbody_energy")
+    return ek.value, ep.value
+
+
+def nbody_energy_ds(ctx):
+    ek, ep = C.c_double(), C.c_double()
+    _check(lib().nbody_energy_ds(ctx, C.byref(ek), C.byref(ep)), "nbody_energy_ds")
     return ek.value, ep.value
 
 

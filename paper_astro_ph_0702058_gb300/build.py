@@ -17,8 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnbody.so")
-SOURCES = ["api.cu", "force.cu", "force_plain.cu", "force_comp.cu", "force_check.cu", "force_sorted.cu", "force_ds.cu", "integrator.cu", "noalloc.cu", "ensemble.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "force.cu", "force_plain.cu", "force_comp.cu", "force_check.cu", "force_sorted.cu", "force_ds.cu", "energy_ds.cu", "integrator.cu", "noalloc.cu", "ensemble.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Per-source nvcc flags (none at present).
+SOURCE_FLAGS: dict[str, list[str]] = {}
 
 
 def nvcc() -> str:
@@ -58,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags
+        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags + SOURCE_FLAGS.get(src, [])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode:
             sys.stderr.write(r.stdout + r.stderr)

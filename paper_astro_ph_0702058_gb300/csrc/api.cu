@@ -291,6 +291,26 @@ int check_params(const nbody_params *p)
     return NBODY_OK;
 }
 
+int energy_common(nbody_ctx *c, double *ekin, double *epot, bool ds_potential)
+{
+    NB_CUDA(time_range_launch(c->S, c->trange, c->s, &c->stats.kernel_launches), "time-range kernel");
+    NB_CUDA(cudaMemcpyAsync(c->trange_host, c->trange, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s),
+            "time-range read-back");
+    int r = sync_and_check(c);
+    if (r != NBODY_OK) return r;
+    if (c->trange_host[0] != c->trange_host[1])
+        return fail(NBODY_ENOTSYNC, "particles are at different times (%llu .. %llu ticks)", c->trange_host[0],
+                    c->trange_host[1]);
+    NB_CUDA(energy_launch(c->S, c->eps2, c->phi, c->e_out, c->s, &c->stats.kernel_launches, ds_potential),
+            "energy kernels");
+    NB_CUDA(cudaMemcpyAsync(c->e_host, c->e_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s), "energy read-back");
+    r = sync_and_check(c);
+    if (r != NBODY_OK) return r;
+    *ekin = c->e_host[0];
+    *epot = c->e_host[1];
+    return NBODY_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -756,21 +776,13 @@ int nbody_sync(nbody_ctx *c)
 int nbody_energy(nbody_ctx *c, double *ekin, double *epot)
 {
     if (!c || !ekin || !epot) return fail(NBODY_EINVAL, "nbody_energy: null argument");
-    NB_CUDA(time_range_launch(c->S, c->trange, c->s, &c->stats.kernel_launches), "time-range kernel");
-    NB_CUDA(cudaMemcpyAsync(c->trange_host, c->trange, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s),
-            "time-range read-back");
-    int r = sync_and_check(c);
-    if (r != NBODY_OK) return r;
-    if (c->trange_host[0] != c->trange_host[1])
-        return fail(NBODY_ENOTSYNC, "particles are at different times (%llu .. %llu ticks)", c->trange_host[0],
-                    c->trange_host[1]);
-    NB_CUDA(energy_launch(c->S, c->eps2, c->phi, c->e_out, c->s, &c->stats.kernel_launches), "energy kernels");
-    NB_CUDA(cudaMemcpyAsync(c->e_host, c->e_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s), "energy read-back");
-    r = sync_and_check(c);
-    if (r != NBODY_OK) return r;
-    *ekin = c->e_host[0];
-    *epot = c->e_host[1];
-    return NBODY_OK;
+    return energy_common(c, ekin, epot, false);
+}
+
+int nbody_energy_ds(nbody_ctx *c, double *ekin, double *epot)
+{
+    if (!c || !ekin || !epot) return fail(NBODY_EINVAL, "nbody_energy_ds: null argument");
+    return energy_common(c, ekin, epot, true);
 }
 
 int nbody_get_state(nbody_ctx *c, double *x, double *v, double *a, double *k, int64_t *t_tick, int8_t *level)

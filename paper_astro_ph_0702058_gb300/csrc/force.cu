@@ -167,6 +167,7 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     P.part = static_cast<float *>(partials);
     P.st = st;
     P.skip_first_copy = g_skip_first_copy;
+    P.opaque_zero = 0;
     cudaError_t e = mode == kModeComp    ? force_dispatch_comp(P, c, s)
                     : mode == kModeCheck ? force_dispatch_check(P, c, s)
                                          : force_dispatch_plain(P, c, s);

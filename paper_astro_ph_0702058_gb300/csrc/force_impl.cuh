@@ -59,6 +59,7 @@ struct ForceParams {
     float *__restrict__ part;  // [split][7 or 14][n_act] when split > 1
     DevStatus *st;
     int skip_first_copy;       // test hook: leave the first tile's copy out
+    unsigned long long opaque_zero;  // always 0; hides values from the assembler (f2_opaque)
 };
 
 // One pair term, Appendix A: dx = x_j - x_i, dv = v_j - v_i, r^2 = eps^2 + dx.dx,
@@ -370,42 +371,44 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
         pot[q] = s;
 }
 
-// Same sums for few rows and many j-ranges: one warp per row, lane l adds the
-// ranges l, l + 32, ... (FP64), then a fixed shuffle tree adds the 32 lanes.
-// Used when the one-thread-per-row version would walk hundreds of ranges.
+// The same sums for many j-ranges: a block holds 32 consecutive rows of one
+// component and 8 warps; warp w adds the ranges w, w + 8, ... of its lane's
+// row (FP64, ascending), so each load of a warp is 32 consecutive floats of one
+// range; then the 8 warp sums of a row are added in warp order.  Grid:
+// (ceil(n_act / 32), 7).
 template <int MODE>
-__global__ void reduce_partials_warp_kernel(const float *__restrict__ part, int split, int n_act,
-                                            double *__restrict__ acc, double *__restrict__ jerk,
-                                            double *__restrict__ pot, const long long *n_act_dev)
+__global__ void __launch_bounds__(256) reduce_partials_2d_kernel(const float *__restrict__ part, int split,
+                                                                 int n_act, double *__restrict__ acc,
+                                                                 double *__restrict__ jerk,
+                                                                 double *__restrict__ pot, const long long *n_act_dev)
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
+    __shared__ double sh[8][32];
     if (n_act_dev) n_act = static_cast<int>(*n_act_dev);
-    const int lane = threadIdx.x & 31;
-    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (q >= n_act) return;
-    double r[7];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) r[c] = 0.0;
-    for (int sp = lane; sp < split; sp += 32) {
-        const float *b = part + static_cast<size_t>(sp) * NC * n_act + q;
-#pragma unroll
-        for (int c = 0; c < 7; ++c) {
-            r[c] += static_cast<double>(b[static_cast<size_t>(c) * n_act]);
-            if (is_ds(MODE)) r[c] += static_cast<double>(b[static_cast<size_t>(7 + c) * n_act]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.y;
+    const int q = blockIdx.x * 32 + lane;
+    if (static_cast<int>(blockIdx.x) * 32 >= n_act) return;  // a launch sized for more rows
+    double r = 0.0;
+    if (q < n_act) {
+        for (int sp = w; sp < split; sp += 8) {
+            const float *b = part + (static_cast<size_t>(sp) * NC + c) * n_act + q;
+            r += static_cast<double>(b[0]);
+            if (is_ds(MODE)) r += static_cast<double>(b[static_cast<size_t>(7) * n_act]);
         }
     }
+    sh[w][lane] = r;
+    __syncthreads();
+    if (w == 0 && q < n_act) {
+        double t = sh[0][lane];
 #pragma unroll
-    for (int c = 0; c < 7; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_down_sync(0xffffffffu, r[c], o);
-    if (lane == 0) {
-        acc[3 * static_cast<size_t>(q) + 0] = r[0];
-        acc[3 * static_cast<size_t>(q) + 1] = r[1];
-        acc[3 * static_cast<size_t>(q) + 2] = r[2];
-        jerk[3 * static_cast<size_t>(q) + 0] = r[3];
-        jerk[3 * static_cast<size_t>(q) + 1] = r[4];
-        jerk[3 * static_cast<size_t>(q) + 2] = r[5];
-        pot[q] = r[6];
+        for (int k = 1; k < 8; ++k) t += sh[k][lane];
+        if (c < 3)
+            acc[3 * static_cast<size_t>(q) + c] = t;
+        else if (c < 6)
+            jerk[3 * static_cast<size_t>(q) + c - 3] = t;
+        else
+            pot[q] = t;
     }
 }
 

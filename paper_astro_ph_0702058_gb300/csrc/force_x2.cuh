@@ -141,6 +141,19 @@ __device__ __forceinline__ void fold_ds_x2(f2_t &hi, f2_t &lo, const f2_t x)
     lo = f2_add(lo, e);
 }
 
+// x ^ z for a z that is zero at run time but unknown to the compiler: the value
+// is unchanged, but it leaves through an integer operation, so the assembler can
+// no longer fuse the packed product that formed x into an instruction that
+// uses it.  Without this it fuses a term's product into the TwoSum that folds
+// the term (even with multiply-add contraction switched off), which keeps the
+// product's own rounding error in the low word.
+__device__ __forceinline__ f2_t f2_opaque(const f2_t x, const unsigned long long z)
+{
+    f2_t r;
+    asm("xor.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(z));
+    return r;
+}
+
 // Summation-check form of pair_term_x2 (kModeCheck): the compensated pair term
 // with the correctly rounded reciprocal square root (per half), every term
 // formed by its own product (no multiply-add into the sums), and each of the
@@ -152,12 +165,14 @@ __device__ __forceinline__ void fold_ds_x2(f2_t &hi, f2_t &lo, const f2_t x)
 //   xv = fma(dz, dvz, fma(dy, dvy, dx * dvx));  mr = m rinv;  mr3 = mr (rinv rinv)
 //   terms: mr3 dx,  mr3 fma(-3 (xv (rinv rinv)), dx, dv),  -mr
 // (x (-3) rounds to the negation of 3 x, so the jerk term is the CPU's bit for bit.)
+// Each term passes through f2_opaque (z = 0) before its fold, so it is folded
+// as the rounded FP32 value.
 template <bool SELF>
 __device__ __forceinline__ void pair_term_x2_check(const f2_t X, const f2_t Y, const f2_t Z, const f2_t M,
                                                    const f2_t VX, const f2_t VY, const f2_t VZ, const f2_t LX,
                                                    const f2_t LY, const f2_t LZ, const I2 &I, const f2_t E2,
-                                                   const f2_t NEG3, const int j_even, const int gi, f2_t (&hi)[7],
-                                                   f2_t (&lo)[7])
+                                                   const f2_t NEG3, const int j_even, const int gi,
+                                                   const unsigned long long z, f2_t (&hi)[7], f2_t (&lo)[7])
 {
     const f2_t dx = f2_add(f2_sub(X, I.x), f2_sub(LX, I.lx));
     const f2_t dy = f2_add(f2_sub(Y, I.y), f2_sub(LY, I.ly));
@@ -177,13 +192,13 @@ __device__ __forceinline__ void pair_term_x2_check(const f2_t X, const f2_t Y, c
     const f2_t mr = f2_mul(M, rinv);
     const f2_t mr3 = f2_mul(mr, rinv2);
     const f2_t wn = f2_mul(f2_mul(xv, rinv2), NEG3);
-    fold_ds_x2(hi[0], lo[0], f2_mul(mr3, dx));
-    fold_ds_x2(hi[1], lo[1], f2_mul(mr3, dy));
-    fold_ds_x2(hi[2], lo[2], f2_mul(mr3, dz));
-    fold_ds_x2(hi[3], lo[3], f2_mul(mr3, f2_fma(wn, dx, dvx)));
-    fold_ds_x2(hi[4], lo[4], f2_mul(mr3, f2_fma(wn, dy, dvy)));
-    fold_ds_x2(hi[5], lo[5], f2_mul(mr3, f2_fma(wn, dz, dvz)));
-    fold_ds_x2(hi[6], lo[6], f2_sub(0ull, mr));
+    fold_ds_x2(hi[0], lo[0], f2_opaque(f2_mul(mr3, dx), z));
+    fold_ds_x2(hi[1], lo[1], f2_opaque(f2_mul(mr3, dy), z));
+    fold_ds_x2(hi[2], lo[2], f2_opaque(f2_mul(mr3, dz), z));
+    fold_ds_x2(hi[3], lo[3], f2_opaque(f2_mul(mr3, f2_fma(wn, dx, dvx)), z));
+    fold_ds_x2(hi[4], lo[4], f2_opaque(f2_mul(mr3, f2_fma(wn, dy, dvy)), z));
+    fold_ds_x2(hi[5], lo[5], f2_opaque(f2_mul(mr3, f2_fma(wn, dz, dvz)), z));
+    fold_ds_x2(hi[6], lo[6], f2_opaque(f2_sub(0ull, mr), z));
 }
 
 // Structure-of-arrays copy of one tile: x y z m vx vy vz (lx ly lz).
@@ -198,7 +213,8 @@ struct SoaTile {
 template <int IPT, bool SELF>
 __device__ __forceinline__ void tile_sums_x2_check(const SoaTile<kModeCheck> &T, const int j0, const I2 (&I)[IPT],
                                                    const int (&gi)[IPT], const f2_t E2, const f2_t NEG3,
-                                                   f2_t (&ph)[IPT][7], f2_t (&pl)[IPT][7])
+                                                   const unsigned long long z, f2_t (&ph)[IPT][7],
+                                                   f2_t (&pl)[IPT][7])
 {
 #pragma unroll 2
     for (int jj = 0; jj < kJTile; jj += 4) {
@@ -214,7 +230,8 @@ __device__ __forceinline__ void tile_sums_x2_check(const SoaTile<kModeCheck> &T,
 #pragma unroll
             for (int u = 0; u < IPT; ++u)
                 pair_term_x2_check<SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h], v[7][h],
-                                         v[8][h], v[9][h], I[u], E2, NEG3, j0 + jj + 2 * h, gi[u], ph[u], pl[u]);
+                                         v[8][h], v[9][h], I[u], E2, NEG3, j0 + jj + 2 * h, gi[u], z, ph[u],
+                                         pl[u]);
     }
 }
 
@@ -416,9 +433,9 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
                 self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
             if constexpr (MODE == kModeCheck) {
                 if (self_tile)
-                    tile_sums_x2_check<IPT, true>(T, j0, I, gi, E2, NEG3, ph, pl);
+                    tile_sums_x2_check<IPT, true>(T, j0, I, gi, E2, NEG3, P.opaque_zero, ph, pl);
                 else
-                    tile_sums_x2_check<IPT, false>(T, j0, I, gi, E2, NEG3, ph, pl);
+                    tile_sums_x2_check<IPT, false>(T, j0, I, gi, E2, NEG3, P.opaque_zero, ph, pl);
             } else if (self_tile) {
                 tile_sums_x2<MODE, IPT, PF, true>(T, j0, I, gi, E2, NEG3, tot, lo);
             } else {

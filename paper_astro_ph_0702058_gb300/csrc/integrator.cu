@@ -485,11 +485,17 @@ cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, Sche
 }
 
 cudaError_t energy_launch(const State &S, double eps2, double *phi, double *out, cudaStream_t s,
-                          int64_t *launches)
+                          int64_t *launches, bool ds_potential)
 {
-    phi_kernel<<<blocks_for(S.n, kETile), kETile, 0, s>>>(S, eps2, phi);
+    if (ds_potential) {
+        const cudaError_t e = phi_ds_launch(S, eps2, phi, s, launches);
+        if (e != cudaSuccess) return e;
+    } else {
+        phi_kernel<<<blocks_for(S.n, kETile), kETile, 0, s>>>(S, eps2, phi);
+        ++*launches;
+    }
     energy_sum_kernel<<<1, 1024, 0, s>>>(S, phi, out);
-    *launches += 2;
+    ++*launches;
     return cudaGetLastError();
 }
 

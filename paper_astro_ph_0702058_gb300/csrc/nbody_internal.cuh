@@ -163,9 +163,13 @@ struct LoopArgs {
 cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, SchedOut *out, void *scratch,
                                  const LoopArgs &la, cudaStream_t s, int64_t *launches);
 
-// E_kin and E_pot (phi scratch: n doubles; out: 2 doubles).
+// E_kin and E_pot (phi scratch: n doubles; out: 2 doubles); the potential in
+// FP64 or, with ds_potential, in double-single arithmetic (energy_ds.cu).
 cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, double *out,
-                          cudaStream_t s, int64_t *launches);
+                          cudaStream_t s, int64_t *launches, bool ds_potential = false);
+// ---- energy_ds.cu ----
+// phi_i = -sum_{j != i} m_j / sqrt(eps2 + |x_j - x_i|^2) in double-single arithmetic (n doubles).
+cudaError_t phi_ds_launch(const State &S, double eps2, double *phi, cudaStream_t s, int64_t *launches);
 // min and max of t over all particles (out: 2 unsigned long long).
 cudaError_t time_range_launch(const State &S, unsigned long long *out, cudaStream_t s,
                               int64_t *launches);

@@ -302,3 +302,29 @@ def test_nonfinite_input_is_reported(torch):
     with pytest.raises(NBodyError) as e:
         Simulation(m, x, v, EPS2)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("n", [3000, 65536])
+def test_energy_ds_matches_oracle(torch, n):
+    """nbody_energy_ds (double-single potential) against the FP64 oracle's energy: E_kin as in
+    nbody_energy (FP64), E_pot within 1e-12 relative; at N = 65536 also against the library's FP64
+    diagnostic.  It refuses unsynchronised states like nbody_energy."""
+    from paper_astro_ph_0702058_gb300 import NBodyError
+    m, x, v = plummer_sphere(n, 5)
+    with _sim(m, x, v) as sim:
+        ek, ep = sim.energy(ds_potential=True)
+        ref_k, ref_p = oracle.energy(m, x, v, EPS2)
+        print(f"\nenergy_ds n={n}: E_pot rel err {abs(ep - ref_p) / abs(ref_p):.2e}")
+        assert abs(ek - ref_k) <= 1e-13 * abs(ref_k) and abs(ep - ref_p) <= 1e-12 * abs(ref_p)
+        if n == 65536:
+            fk, fp = sim.energy()
+            assert fk == ek and abs(fp - ep) <= 1e-12 * abs(fp)
+        blk = np.zeros(n, dtype=np.int32)
+        t_blk, n_act = sim.next_block(blk)
+        sim.predict(t_blk)
+        sim.force(blk[:n_act])
+        sim.correct(blk[:n_act])
+        if n_act < n:
+            with pytest.raises(NBodyError) as e:
+                sim.energy(ds_potential=True)
+            assert e.value.code == -6

@@ -27,7 +27,9 @@ def _worker(rank, world, port, q):
     bench.barrier(ws)
     t = bench.max_over_ranks(100.0 + 50.0 * rank, ws)
     w = bench.sum_over_ranks(1000.0 * (rank + 1), ws)
-    q.put((r, local, t, w))
+    # every reduction of the benchmark, as each rank calls it (a rank-only call would hang the others)
+    tot = bench.replica_totals(ws, {"comp": 10.0 + rank, "plain": 20.0 - rank}, 30.0 + 5 * rank, 1e12)
+    q.put((r, local, t, w, tot))
     dist.destroy_process_group()
 
 
@@ -46,6 +48,10 @@ def test_two_rank_aggregation():
     assert [g[0] for g in got] == [0, 1] and [g[1] for g in got] == [0, 1]
     assert all(g[2] == 150.0 for g in got)       # slowest rank's time
     assert all(g[3] == 3000.0 for g in got)      # total work of all replicas
+    for g in got:
+        tot = g[4]
+        assert tot["comp"] == {"t_max": 11.0, "pairs": 2e12} and tot["plain"] == {"t_max": 20.0, "pairs": 2e12}
+        assert tot["e2e"] == {"t_max": 35.0, "pairs": 2e12}
 
 
 def test_single_process_is_identity():
