@@ -98,14 +98,9 @@ def rollout(m, x0, v0, eps2, dt, steps):
     return states
 
 
-def rollout_grad(m, x0, v0, eps2, dt, steps):
-    """(L, dL/dx0, dL/dv0, dL/dm) by reverse mode through the whole rollout."""
-    m = np.asarray(m, float)
-    states = rollout(m, x0, v0, eps2, dt, steps)
-    xf = states[-1][0]
-    L = loss(m, xf, eps2)
-    gx, gm = loss_grad(m, xf, eps2)
-    gv = np.zeros_like(gx)
+def _reverse(m, states, eps2, dt, steps, gx, gv, gm):
+    """The reverse sweep from the gradients (gx, gv, gm) of the final x, v and of the masses to
+    (dx0, dv0, dm): corrector, force and predictor transposed step by step, then the t = 0 force."""
     ga = np.zeros_like(gx)
     gk = np.zeros_like(gx)
     c1, c2, c3, c4 = dt ** 4 / 24.0, dt ** 5 / 120.0, dt ** 3 / 6.0, dt ** 4 / 24.0
@@ -133,4 +128,24 @@ def rollout_grad(m, x0, v0, eps2, dt, steps):
         gk = g_k + g_xp * dt ** 3 / 6.0 + g_vp * dt ** 2 / 2.0
     # initial force
     fx, fv, fm = force_vjp(m, states[0][0], states[0][1], eps2, ga, gk)
-    return L, gx + fx, gv + fv, gm + fm
+    return gx + fx, gv + fv, gm + fm
+
+
+def rollout_grad(m, x0, v0, eps2, dt, steps):
+    """(L, dL/dx0, dL/dv0, dL/dm) by reverse mode through the whole rollout."""
+    m = np.asarray(m, float)
+    states = rollout(m, x0, v0, eps2, dt, steps)
+    xf = states[-1][0]
+    L = loss(m, xf, eps2)
+    gx, gm = loss_grad(m, xf, eps2)
+    return (L,) + _reverse(m, states, eps2, dt, steps, gx, np.zeros_like(gx), gm)
+
+
+def rollout_vjp(m, x0, v0, eps2, dt, steps, g_xT, g_vT):
+    """(x_T, v_T, g_x0, g_v0, g_m): the final state of the rollout and the vector-Jacobian product of
+    (x0, v0, m) -> (x_T, v_T) with the cotangents (g_xT, g_vT) of the final positions and velocities."""
+    m = np.asarray(m, float)
+    states = rollout(m, x0, v0, eps2, dt, steps)
+    gx = np.array(g_xT, float).reshape(-1, 3)
+    gv = np.array(g_vT, float).reshape(-1, 3)
+    return (states[-1][0], states[-1][1]) + _reverse(m, states, eps2, dt, steps, gx, gv, np.zeros_like(m))

@@ -81,3 +81,35 @@ def test_force_vjp_matches_central_differences_of_the_c_force():
             fd[idx] = (S(args_p["m"], args_p["x"], args_p["v"]) - S(args_q["m"], args_q["x"], args_q["v"])) / (2 * h)
         err = np.abs(fd - g.reshape(-1)).max() / np.abs(g).max()
         assert err < 1e-7, (name, err)
+
+
+def test_rollout_vjp_matches_central_differences():
+    """The reverse sweep seeded with arbitrary cotangents of the final positions and velocities:
+    <g_x0, dx0> + <g_v0, dv0> + <g_m, dm> against central differences of
+    S = <g_xT, x_T> + <g_vT, v_T> from the C oracle's forward run, for every input component."""
+    n, steps = 8, 16
+    m, x, v = plummer_sphere(n, 51)
+    rng = np.random.default_rng(51)
+    m = m * rng.uniform(0.7, 1.3, n)
+    g_xT, g_vT = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+    xT, vT, gx, gv, gm = adjoint.rollout_vjp(m, x, v, EPS2, 2.0 ** -LEVEL, steps, g_xT, g_vT)
+    st = _c_loss(m, x, v, steps)[1]
+    assert np.abs(xT - st.x).max() <= 1e-12 and np.abs(vT - st.v).max() <= 1e-11
+
+    def S(mm, xx, vv):
+        s = _c_loss(mm, xx, vv, steps)[1]
+        return float((g_xT * s.x).sum() + (g_vT * s.v).sum())
+
+    h = 1e-6
+    for name, arr, g in (("x", x, gx), ("v", v, gv), ("m", m, gm)):
+        fd = np.zeros(arr.size)
+        for idx in range(arr.size):
+            p = arr.reshape(-1).copy(); p[idx] += h  # noqa: E702
+            q = arr.reshape(-1).copy(); q[idx] -= h  # noqa: E702
+            args_p = {"m": m, "x": x, "v": v}
+            args_q = dict(args_p)
+            args_p[name] = p.reshape(arr.shape)
+            args_q[name] = q.reshape(arr.shape)
+            fd[idx] = (S(args_p["m"], args_p["x"], args_p["v"]) - S(args_q["m"], args_q["x"], args_q["v"])) / (2 * h)
+        err = np.abs(fd - g.reshape(-1)).max() / np.abs(g).max()
+        assert err < 1e-6, (name, err)

@@ -79,6 +79,8 @@ ADJ_MUTANTS = {
     "vjp_roles_swapped": ("gx = gd.sum(0) - gd.sum(1)", "gx = gd.sum(1) - gd.sum(0)"),
     "vjp_mass_drop_egk": ("gm = (R3 * dga + R3 * egk", "gm = (R3 * dga + 0.0 * egk"),
     "loss_grad_no_pot": ("gx = 2.0 * x - m[:, None]", "gx = 2.0 * x - 0.0 * m[:, None]"),
+    "vjp_seed_drops_velocity": ("gv = np.array(g_vT, float).reshape(-1, 3)", "gv = 0.0 * np.array(g_vT, float).reshape(-1, 3)"),
+    "reverse_predictor_dt2": ("ga = g_a + g_xp * dt ** 2 / 2.0 + g_vp * dt", "ga = g_a + g_xp * dt ** 2 + g_vp * dt"),
 }
 
 
