@@ -292,6 +292,25 @@ int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const doubl
                        int level, int64_t steps, int64_t checkpoint_every, int mode, double *loss,
                        double *g_x0, double *g_v0, double *g_m, void *stream);
 
+/* The rollout above as a function (x0, v0, m) -> (x_T, v_T): the final
+ * positions and velocities (n x 3, host or device; either may be NULL, not
+ * both).  Allocates its own context; waits.  Errors: as nbody_diff_rollout. */
+int nbody_rollout(int64_t n, const double *m, const double *x0, const double *v0, double eps2,
+                  int level, int64_t steps, int mode, double *x_T, double *v_T, void *stream);
+
+/* Vector-Jacobian product of nbody_rollout: given cotangents g_xT, g_vT of
+ * the final positions and velocities (n x 3, host or device; NULL means
+ * zero), writes g_x0 = (dx_T/dx0)^T g_xT + (dv_T/dx0)^T g_vT, and likewise
+ * g_v0 (n x 3) and g_m (n) (host or device; NULL outputs are skipped, not all
+ * three).  The same checkpointed reverse sweep as nbody_diff_rollout (the
+ * transposed corrector and predictor of Sect. 2 and the hand-written
+ * vector-Jacobian product of Eq. Force), seeded with the cotangents instead of
+ * the loss gradient; the forward run is recomputed inside.  Errors: as
+ * nbody_diff_rollout. */
+int nbody_rollout_vjp(int64_t n, const double *m, const double *x0, const double *v0, double eps2,
+                      int level, int64_t steps, int64_t checkpoint_every, int mode, const double *g_xT,
+                      const double *g_vT, double *g_x0, double *g_v0, double *g_m, void *stream);
+
 /* ---------------------------------------------------------------- ensembles
  * Many independent clusters integrated together: each cluster runs the block-
  * step scheme of Sect. 2 with its own schedule (its own t_blk and block), and

@@ -42,7 +42,7 @@ EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_pred
            "nbody_debug_fail_alloc", "nbody_debug_skip_tile_copy", "nbody_debug_step_graphs", "nbody_force_noalloc",
            "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
            "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_ens_free",
-           "nbody_diff_rollout")
+           "nbody_diff_rollout", "nbody_rollout", "nbody_rollout_vjp")
 
 
 class nbody_params(C.Structure):
@@ -121,6 +121,11 @@ def lib():
             L.nbody_diff_rollout.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int, C.c_int64, C.c_int64, C.c_int,
                                              P, P, P, P, P]
             L.nbody_diff_rollout.restype = C.c_int
+            L.nbody_rollout.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int, C.c_int64, C.c_int, P, P, P]
+            L.nbody_rollout.restype = C.c_int
+            L.nbody_rollout_vjp.argtypes = [C.c_int64, P, P, P, C.c_double, C.c_int, C.c_int64, C.c_int64, C.c_int,
+                                            P, P, P, P, P, P]
+            L.nbody_rollout_vjp.restype = C.c_int
             L.nbody_ens_free.argtypes = [P]
             L.nbody_ens_free.restype = None
             for name in ("nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step",
@@ -361,3 +366,19 @@ def nbody_diff_rollout(n: int, m, x0, v0, eps2: float, level: int, steps: int, c
                                     float(eps2), int(level), int(steps), int(checkpoint_every), int(mode),
                                     ptr(loss, "f64", 1), ptr(g_x0, "f64", 3 * n), ptr(g_v0, "f64", 3 * n),
                                     ptr(g_m, "f64", n), st), "nbody_diff_rollout")
+
+
+def nbody_rollout(n: int, m, x0, v0, eps2: float, level: int, steps: int, mode: int, x_T, v_T, stream=None) -> None:
+    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().nbody_rollout(int(n), ptr(m, "f64", n), ptr(x0, "f64", 3 * n), ptr(v0, "f64", 3 * n), float(eps2),
+                               int(level), int(steps), int(mode), ptr(x_T, "f64", 3 * n), ptr(v_T, "f64", 3 * n), st),
+           "nbody_rollout")
+
+
+def nbody_rollout_vjp(n: int, m, x0, v0, eps2: float, level: int, steps: int, checkpoint_every: int, mode: int,
+                      g_xT, g_vT, g_x0, g_v0, g_m, stream=None) -> None:
+    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().nbody_rollout_vjp(int(n), ptr(m, "f64", n), ptr(x0, "f64", 3 * n), ptr(v0, "f64", 3 * n),
+                                   float(eps2), int(level), int(steps), int(checkpoint_every), int(mode),
+                                   ptr(g_xT, "f64", 3 * n), ptr(g_vT, "f64", 3 * n), ptr(g_x0, "f64", 3 * n),
+                                   ptr(g_v0, "f64", 3 * n), ptr(g_m, "f64", n), st), "nbody_rollout_vjp")

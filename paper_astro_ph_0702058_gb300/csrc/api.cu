@@ -311,6 +311,186 @@ int energy_common(nbody_ctx *c, double *ekin, double *epot, bool ds_potential)
     return NBODY_OK;
 }
 
+// A shared-step rollout (the force at t = 0, then `steps` Hermite steps of dt = 2^-level) and, with
+// `backward`, the reverse sweep: seeded with the loss L = sum |x|^2 + E_pot (seed_loss) or with the
+// cotangents g_xT, g_vT of the final positions and velocities (either may be NULL: zero).  Outputs
+// that are NULL are not written.
+int rollout_impl(const char *who, int64_t n, const double *m, const double *x0, const double *v0, double eps2,
+                 int level, int64_t steps, int64_t checkpoint_every, int mode, bool backward, bool seed_loss,
+                 const double *g_xT, const double *g_vT, double *loss, double *x_T, double *v_T, double *g_x0,
+                 double *g_v0, double *g_m, void *stream)
+{
+    g_err[0] = '\0';
+    if (!m || !x0 || !v0) return fail(NBODY_EINVAL, "%s: null argument", who);
+    if (!(eps2 > 0.0)) return fail(NBODY_EINVAL, "%s: eps2 must be > 0", who);
+    if (level < 0 || level > 40 || steps < 0) return fail(NBODY_EINVAL, "%s: bad level or steps", who);
+    if (checkpoint_every <= 0) checkpoint_every = 16;
+    nbody_params p;
+    nbody_default_params(&p);
+    p.lmin = p.lmax = level;  // one shared power-of-two step: every block is all particles
+    p.mode = mode;
+    p.stream = stream;
+    nbody_ctx *c = nullptr;
+    int r = nbody_init(&c, n, m, x0, v0, eps2, &p);
+    if (r != NBODY_OK) return r;
+    const size_t nd = static_cast<size_t>(n);
+    const size_t npad = static_cast<size_t>(c->n_pad);
+    const int64_t n_ck = steps / checkpoint_every + 1;
+    const size_t state_doubles = 12 * nd;  // x, v, a, k (contiguous after m)
+    double *ck = nullptr, *seg = nullptr, *gbuf = nullptr, *lval = nullptr, *dloss = nullptr, *vjp = nullptr;
+    float4 *g4 = nullptr;
+    DiffGrads G{};
+    const double dt = std::ldexp(1.0, -level);
+    const float e2 = static_cast<float>(eps2);
+    cudaStream_t s = c->s;
+    int64_t *L = &c->stats.kernel_launches;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        void *bufs[] = {ck, seg, gbuf, lval, dloss, g4, vjp};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        nbody_free(c);
+        return code;
+    };
+#define NB_DR(call, what)                                     \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return done(cuda_fail(e_, what)); \
+    } while (0)
+    // the state after the last step, copied out row-major
+    auto copy_final = [&]() -> int {
+        if (x_T) {
+            NB_CUDA(soa_to_aos_launch(c->S.x[0], c->S.x[1], c->S.x[2], c->stage, n, s, L), "layout");
+            NB_CUDA(cudaMemcpyAsync(x_T, c->stage, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "state copy");
+        }
+        if (v_T) {
+            NB_CUDA(soa_to_aos_launch(c->S.v[0], c->S.v[1], c->S.v[2], c->stage + 3 * nd, n, s, L), "layout");
+            NB_CUDA(cudaMemcpyAsync(v_T, c->stage + 3 * nd, 3 * nd * sizeof(double), cudaMemcpyDefault, s),
+                    "state copy");
+        }
+        return NBODY_OK;
+    };
+    if (!backward) {
+        NB_DR(iota_launch(c->act_force, n, s, L), "index kernel");
+        for (int64_t k = 0; k < steps; ++k) {
+            r = predict_internal(c, k + 1);
+            if (r == NBODY_OK) r = force_internal(c, n);
+            if (r == NBODY_OK) r = correct_internal(c, c->act_force, n, c->f_acc, c->f_jerk);
+            if (r != NBODY_OK) return done(r);
+        }
+        r = copy_final();
+        if (r == NBODY_OK) r = sync_and_check(c);
+        return done(r);
+    }
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&ck), n_ck * state_doubles * sizeof(double)), "checkpoints");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&seg), checkpoint_every * state_doubles * sizeof(double)), "segment");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&gbuf), 19 * nd * sizeof(double)), "gradients");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&lval), nd * sizeof(double)), "loss terms");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&dloss), sizeof(double)), "loss");
+    NB_DR(dev_alloc(reinterpret_cast<void **>(&g4), 2 * npad * sizeof(float4)), "force upstream");
+    const size_t vjp_doubles = vjp_scratch_doubles(n, c->n_pad, c->sm_count);
+    if (vjp_doubles) NB_DR(dev_alloc(reinterpret_cast<void **>(&vjp), vjp_doubles * sizeof(double)), "adjoint scratch");
+    NB_DR(cudaMemsetAsync(gbuf, 0, 19 * nd * sizeof(double), s), "memset");
+    NB_DR(cudaMemsetAsync(g4, 0, 2 * npad * sizeof(float4), s), "memset");
+    for (int q = 0; q < 3; ++q) {
+        G.gx[q] = gbuf + (0 + q) * nd;
+        G.gv[q] = gbuf + (3 + q) * nd;
+        G.ga[q] = gbuf + (6 + q) * nd;
+        G.gk[q] = gbuf + (9 + q) * nd;
+        G.gxp[q] = gbuf + (12 + q) * nd;
+        G.gvp[q] = gbuf + (15 + q) * nd;
+    }
+    G.gm = gbuf + 18 * nd;
+    G.gA = g4;
+    G.gK = g4 + npad;
+    double *xvak = c->state + nd;  // x[3], v[3], a[3], k[3]
+    NB_DR(iota_launch(c->act_force, n, s, L), "index kernel");
+    // one shared Hermite step from tick s0 to s0 + 1 (all particles in the block)
+    auto step = [&](int64_t s0) -> int {
+        int rr = predict_internal(c, s0 + 1);
+        if (rr != NBODY_OK) return rr;
+        rr = force_internal(c, n);
+        if (rr != NBODY_OK) return rr;
+        return correct_internal(c, c->act_force, n, c->f_acc, c->f_jerk);
+    };
+    auto restore = [&](const double *src, int64_t tick) -> int {
+        NB_CUDA(cudaMemcpyAsync(xvak, src, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "restore");
+        NB_CUDA(set_time_launch(c->S, tick, level, s, L), "time kernel");
+        c->t_max = tick;
+        return NBODY_OK;
+    };
+    // forward with checkpoints
+    NB_DR(cudaMemcpyAsync(ck, xvak, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "checkpoint");
+    for (int64_t k = 0; k < steps; ++k) {
+        r = step(k);
+        if (r != NBODY_OK) return done(r);
+        if ((k + 1) % checkpoint_every == 0)
+            NB_DR(cudaMemcpyAsync(ck + ((k + 1) / checkpoint_every) * state_doubles, xvak,
+                                  state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                  "checkpoint");
+    }
+    r = copy_final();  // before the backward sweep overwrites the state
+    if (r != NBODY_OK) return done(r);
+    if (seed_loss) {
+        NB_DR(loss_launch(c->S, eps2, G, lval, dloss, s, L), "loss kernels");
+    } else {  // the cotangents of the final x, v seed the sweep (row-major n x 3 -> components)
+        if (g_xT) {
+            NB_DR(to_device(c->stage, g_xT, 3 * nd * sizeof(double), s), "cotangent upload");
+            NB_DR(aos_to_soa_launch(c->stage, G.gx[0], G.gx[1], G.gx[2], n, s, L), "layout kernel");
+        }
+        if (g_vT) {
+            NB_DR(to_device(c->stage + 3 * nd, g_vT, 3 * nd * sizeof(double), s), "cotangent upload");
+            NB_DR(aos_to_soa_launch(c->stage + 3 * nd, G.gv[0], G.gv[1], G.gv[2], n, s, L), "layout kernel");
+        }
+    }
+    // backward, one checkpoint segment at a time
+    for (int64_t seg0 = (steps - 1) / checkpoint_every * checkpoint_every; steps > 0 && seg0 >= 0;
+         seg0 -= checkpoint_every) {
+        const int64_t seg1 = std::min(seg0 + checkpoint_every, steps);
+        r = restore(ck + (seg0 / checkpoint_every) * state_doubles, seg0);
+        if (r != NBODY_OK) return done(r);
+        for (int64_t k = seg0; k < seg1; ++k) {
+            NB_DR(cudaMemcpyAsync(seg + (k - seg0) * state_doubles, xvak, state_doubles * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, s),
+                  "segment");
+            if (k + 1 < seg1) {
+                r = step(k);
+                if (r != NBODY_OK) return done(r);
+            }
+        }
+        for (int64_t k = seg1 - 1; k >= seg0; --k) {
+            r = restore(seg + (k - seg0) * state_doubles, k);
+            if (r != NBODY_OK) return done(r);
+            r = predict_internal(c, k + 1);  // j-stream at the predicted state of step k
+            if (r != NBODY_OK) return done(r);
+            NB_DR(adj_correct_launch(G, n, dt, s, L), "adjoint corrector");
+            NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
+            NB_DR(adj_predict_launch(G, n, dt, s, L), "adjoint predictor");
+        }
+    }
+    // the t = 0 force
+    r = restore(ck, 0);
+    if (r != NBODY_OK) return done(r);
+    r = predict_internal(c, 0);
+    if (r != NBODY_OK) return done(r);
+    NB_DR(adj_init_launch(G, n, s, L), "adjoint init");
+    NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
+    if (seed_loss && loss) NB_DR(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDefault, s), "loss copy");
+    if (g_x0) {
+        NB_DR(soa_to_aos_launch(G.gxp[0], G.gxp[1], G.gxp[2], c->stage, n, s, L), "layout");
+        NB_DR(cudaMemcpyAsync(g_x0, c->stage, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
+    }
+    if (g_v0) {
+        NB_DR(soa_to_aos_launch(G.gvp[0], G.gvp[1], G.gvp[2], c->stage + 3 * nd, n, s, L), "layout");
+        NB_DR(cudaMemcpyAsync(g_v0, c->stage + 3 * nd, 3 * nd * sizeof(double), cudaMemcpyDefault, s),
+              "gradient copy");
+    }
+    if (g_m) NB_DR(cudaMemcpyAsync(g_m, G.gm, nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
+    r = sync_and_check(c);
+#undef NB_DR
+    return done(r);
+}
+
 }  // namespace
 
 extern "C" {
@@ -860,136 +1040,31 @@ int nbody_get_stats(nbody_ctx *c, nbody_stats *s)
     return NBODY_OK;
 }
 
+
 int nbody_diff_rollout(int64_t n, const double *m, const double *x0, const double *v0, double eps2, int level,
                        int64_t steps, int64_t checkpoint_every, int mode, double *loss, double *g_x0,
                        double *g_v0, double *g_m, void *stream)
 {
-    g_err[0] = '\0';
-    if (!m || !x0 || !v0 || !loss || !g_x0 || !g_v0 || !g_m) return fail(NBODY_EINVAL, "nbody_diff_rollout: null argument");
-    if (!(eps2 > 0.0)) return fail(NBODY_EINVAL, "nbody_diff_rollout: eps2 must be > 0");
-    if (level < 0 || level > 40 || steps < 0) return fail(NBODY_EINVAL, "nbody_diff_rollout: bad level or steps");
-    if (checkpoint_every <= 0) checkpoint_every = 16;
-    nbody_params p;
-    nbody_default_params(&p);
-    p.lmin = p.lmax = level;  // one shared power-of-two step: every block is all particles
-    p.mode = mode;
-    p.stream = stream;
-    nbody_ctx *c = nullptr;
-    int r = nbody_init(&c, n, m, x0, v0, eps2, &p);
-    if (r != NBODY_OK) return r;
-    const size_t nd = static_cast<size_t>(n);
-    const size_t npad = static_cast<size_t>(c->n_pad);
-    const int64_t n_ck = steps / checkpoint_every + 1;
-    const size_t state_doubles = 12 * nd;  // x, v, a, k (contiguous after m)
-    double *ck = nullptr, *seg = nullptr, *gbuf = nullptr, *lval = nullptr, *dloss = nullptr, *vjp = nullptr;
-    float4 *g4 = nullptr;
-    DiffGrads G{};
-    const double dt = std::ldexp(1.0, -level);
-    const float e2 = static_cast<float>(eps2);
-    cudaStream_t s = c->s;
-    int64_t *L = &c->stats.kernel_launches;
-    auto done = [&](int code) {
-        cudaStreamSynchronize(s);
-        void *bufs[] = {ck, seg, gbuf, lval, dloss, g4, vjp};
-        for (void *b : bufs)
-            if (b) cudaFree(b);
-        nbody_free(c);
-        return code;
-    };
-#define NB_DR(call, what)                                     \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return done(cuda_fail(e_, what)); \
-    } while (0)
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&ck), n_ck * state_doubles * sizeof(double)), "checkpoints");
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&seg), checkpoint_every * state_doubles * sizeof(double)), "segment");
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&gbuf), 19 * nd * sizeof(double)), "gradients");
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&lval), nd * sizeof(double)), "loss terms");
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&dloss), sizeof(double)), "loss");
-    NB_DR(dev_alloc(reinterpret_cast<void **>(&g4), 2 * npad * sizeof(float4)), "force upstream");
-    const size_t vjp_doubles = vjp_scratch_doubles(n, c->n_pad, c->sm_count);
-    if (vjp_doubles) NB_DR(dev_alloc(reinterpret_cast<void **>(&vjp), vjp_doubles * sizeof(double)), "adjoint scratch");
-    NB_DR(cudaMemsetAsync(gbuf, 0, 19 * nd * sizeof(double), s), "memset");
-    NB_DR(cudaMemsetAsync(g4, 0, 2 * npad * sizeof(float4), s), "memset");
-    for (int q = 0; q < 3; ++q) {
-        G.gx[q] = gbuf + (0 + q) * nd;
-        G.gv[q] = gbuf + (3 + q) * nd;
-        G.ga[q] = gbuf + (6 + q) * nd;
-        G.gk[q] = gbuf + (9 + q) * nd;
-        G.gxp[q] = gbuf + (12 + q) * nd;
-        G.gvp[q] = gbuf + (15 + q) * nd;
-    }
-    G.gm = gbuf + 18 * nd;
-    G.gA = g4;
-    G.gK = g4 + npad;
-    double *xvak = c->state + nd;  // x[3], v[3], a[3], k[3]
-    NB_DR(iota_launch(c->act_force, n, s, L), "index kernel");
-    // one shared Hermite step from tick s0 to s0 + 1 (all particles in the block)
-    auto step = [&](int64_t s0) -> int {
-        int rr = predict_internal(c, s0 + 1);
-        if (rr != NBODY_OK) return rr;
-        rr = force_internal(c, n);
-        if (rr != NBODY_OK) return rr;
-        return correct_internal(c, c->act_force, n, c->f_acc, c->f_jerk);
-    };
-    auto restore = [&](const double *src, int64_t tick) -> int {
-        NB_CUDA(cudaMemcpyAsync(xvak, src, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "restore");
-        NB_CUDA(set_time_launch(c->S, tick, level, s, L), "time kernel");
-        c->t_max = tick;
-        return NBODY_OK;
-    };
-    // forward with checkpoints
-    NB_DR(cudaMemcpyAsync(ck, xvak, state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "checkpoint");
-    for (int64_t k = 0; k < steps; ++k) {
-        r = step(k);
-        if (r != NBODY_OK) return done(r);
-        if ((k + 1) % checkpoint_every == 0)
-            NB_DR(cudaMemcpyAsync(ck + ((k + 1) / checkpoint_every) * state_doubles, xvak,
-                                  state_doubles * sizeof(double), cudaMemcpyDeviceToDevice, s),
-                  "checkpoint");
-    }
-    NB_DR(loss_launch(c->S, eps2, G, lval, dloss, s, L), "loss kernels");
-    // backward, one checkpoint segment at a time
-    for (int64_t seg0 = (steps - 1) / checkpoint_every * checkpoint_every; steps > 0 && seg0 >= 0;
-         seg0 -= checkpoint_every) {
-        const int64_t seg1 = std::min(seg0 + checkpoint_every, steps);
-        r = restore(ck + (seg0 / checkpoint_every) * state_doubles, seg0);
-        if (r != NBODY_OK) return done(r);
-        for (int64_t k = seg0; k < seg1; ++k) {
-            NB_DR(cudaMemcpyAsync(seg + (k - seg0) * state_doubles, xvak, state_doubles * sizeof(double),
-                                  cudaMemcpyDeviceToDevice, s),
-                  "segment");
-            if (k + 1 < seg1) {
-                r = step(k);
-                if (r != NBODY_OK) return done(r);
-            }
-        }
-        for (int64_t k = seg1 - 1; k >= seg0; --k) {
-            r = restore(seg + (k - seg0) * state_doubles, k);
-            if (r != NBODY_OK) return done(r);
-            r = predict_internal(c, k + 1);  // j-stream at the predicted state of step k
-            if (r != NBODY_OK) return done(r);
-            NB_DR(adj_correct_launch(G, n, dt, s, L), "adjoint corrector");
-            NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
-            NB_DR(adj_predict_launch(G, n, dt, s, L), "adjoint predictor");
-        }
-    }
-    // the t = 0 force
-    r = restore(ck, 0);
-    if (r != NBODY_OK) return done(r);
-    r = predict_internal(c, 0);
-    if (r != NBODY_OK) return done(r);
-    NB_DR(adj_init_launch(G, n, s, L), "adjoint init");
-    NB_DR(force_vjp_launch(c->J, G, n, e2, c->sm_count, vjp, s, L), "force adjoint");
-    NB_DR(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDefault, s), "loss copy");
-    NB_DR(soa_to_aos_launch(G.gxp[0], G.gxp[1], G.gxp[2], c->stage, n, s, L), "layout");
-    NB_DR(cudaMemcpyAsync(g_x0, c->stage, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
-    NB_DR(soa_to_aos_launch(G.gvp[0], G.gvp[1], G.gvp[2], c->stage + 3 * nd, n, s, L), "layout");
-    NB_DR(cudaMemcpyAsync(g_v0, c->stage + 3 * nd, 3 * nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
-    NB_DR(cudaMemcpyAsync(g_m, G.gm, nd * sizeof(double), cudaMemcpyDefault, s), "gradient copy");
-    r = sync_and_check(c);
-#undef NB_DR
-    return done(r);
+    if (!loss || !g_x0 || !g_v0 || !g_m) return fail(NBODY_EINVAL, "nbody_diff_rollout: null argument");
+    return rollout_impl("nbody_diff_rollout", n, m, x0, v0, eps2, level, steps, checkpoint_every, mode, true, true,
+                        nullptr, nullptr, loss, nullptr, nullptr, g_x0, g_v0, g_m, stream);
+}
+
+int nbody_rollout(int64_t n, const double *m, const double *x0, const double *v0, double eps2, int level,
+                  int64_t steps, int mode, double *x_T, double *v_T, void *stream)
+{
+    if (!x_T && !v_T) return fail(NBODY_EINVAL, "nbody_rollout: no output");
+    return rollout_impl("nbody_rollout", n, m, x0, v0, eps2, level, steps, 0, mode, false, false, nullptr, nullptr,
+                        nullptr, x_T, v_T, nullptr, nullptr, nullptr, stream);
+}
+
+int nbody_rollout_vjp(int64_t n, const double *m, const double *x0, const double *v0, double eps2, int level,
+                      int64_t steps, int64_t checkpoint_every, int mode, const double *g_xT, const double *g_vT,
+                      double *g_x0, double *g_v0, double *g_m, void *stream)
+{
+    if (!g_x0 && !g_v0 && !g_m) return fail(NBODY_EINVAL, "nbody_rollout_vjp: no output");
+    return rollout_impl("nbody_rollout_vjp", n, m, x0, v0, eps2, level, steps, checkpoint_every, mode, true, false,
+                        g_xT, g_vT, nullptr, nullptr, nullptr, g_x0, g_v0, g_m, stream);
 }
 
 void nbody_free(nbody_ctx *c)

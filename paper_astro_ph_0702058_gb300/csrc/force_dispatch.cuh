@@ -97,7 +97,7 @@ cudaError_t reduce_launch(const float *part, int split, int n_act, double *acc, 
 {
     const int nt = 256;
     if (split >= 8)
-        reduce_partials_2d_kernel<MODE><<<dim3(static_cast<unsigned>((n_act + 31) / 32), 7), nt, 0, s>>>(
+        reduce_partials_2d_kernel<MODE, 8><<<dim3(static_cast<unsigned>((n_act + 7) / 8), 7), nt, 0, s>>>(
             part, split, n_act, acc, jerk, pot, n_act_dev);
     else
         reduce_partials_kernel<MODE><<<static_cast<unsigned>((7LL * n_act + nt - 1) / nt), nt, 0, s>>>(

@@ -371,38 +371,40 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
         pot[q] = s;
 }
 
-// The same sums for many j-ranges: a block holds 32 consecutive rows of one
-// component and 8 warps; warp w adds the ranges w, w + 8, ... of its lane's
-// row (FP64, ascending), so each load of a warp is 32 consecutive floats of one
-// range; then the 8 warp sums of a row are added in warp order.  Grid:
-// (ceil(n_act / 32), 7).
-template <int MODE>
+// The same sums for many j-ranges: a block of 256 threads holds 8 consecutive
+// rows of one component and 32 lanes per row; lane w adds the ranges w, w + 32,
+// ... of its row (FP64, ascending), so a warp loads 8 consecutive floats (one
+// 32-byte sector) of each of 4 ranges, and a row's ranges are spread over 32
+// lanes.  The lane sums of a row are then added in lane order.  The order
+// depends on the split only, not on the number of rows a launch is sized for.
+// Grid: (ceil(n_act / 8), 7).
+template <int MODE, int R>
 __global__ void __launch_bounds__(256) reduce_partials_2d_kernel(const float *__restrict__ part, int split,
                                                                  int n_act, double *__restrict__ acc,
                                                                  double *__restrict__ jerk,
                                                                  double *__restrict__ pot, const long long *n_act_dev)
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
-    __shared__ double sh[8][32];
+    constexpr int L = 256 / R;  // lanes per row
+    __shared__ double sh[L][R];
     if (n_act_dev) n_act = static_cast<int>(*n_act_dev);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = threadIdx.x % R, w = threadIdx.x / R;
     const int c = blockIdx.y;
-    const int q = blockIdx.x * 32 + lane;
-    if (static_cast<int>(blockIdx.x) * 32 >= n_act) return;  // a launch sized for more rows
+    const int q = blockIdx.x * R + row;
+    if (static_cast<int>(blockIdx.x) * R >= n_act) return;  // a launch sized for more rows
     double r = 0.0;
     if (q < n_act) {
-        for (int sp = w; sp < split; sp += 8) {
+        for (int sp = w; sp < split; sp += L) {
             const float *b = part + (static_cast<size_t>(sp) * NC + c) * n_act + q;
             r += static_cast<double>(b[0]);
             if (is_ds(MODE)) r += static_cast<double>(b[static_cast<size_t>(7) * n_act]);
         }
     }
-    sh[w][lane] = r;
+    sh[w][row] = r;
     __syncthreads();
     if (w == 0 && q < n_act) {
-        double t = sh[0][lane];
-#pragma unroll
-        for (int k = 1; k < 8; ++k) t += sh[k][lane];
+        double t = sh[0][row];
+        for (int k = 1; k < L; ++k) t += sh[k][row];
         if (c < 3)
             acc[3 * static_cast<size_t>(q) + c] = t;
         else if (c < 6)

@@ -1,6 +1,7 @@
 // Throughput probes of the GPU pipes that bound the pair loop: chains of
 // FP32 FMA, ADD and MUL, the packed FP32x2 FMA, and the MUFU reciprocal
-// square root.  A standalone program (not part of libnbody.so); prints one
+// square root; and of the pipes that bound the FP64 predictor and corrector:
+// FP64 FMA and the double -> float -> double conversions.  A standalone program (not part of libnbody.so); prints one
 // JSON line with results per SM and clock, the clock taken from clock64()
 // over the kernel's own duration.
 #include <cstdio>
@@ -90,6 +91,28 @@ __global__ void mufu_chain(float *out, long long *cyc, int iters)
     if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - c0;
 }
 
+// FP64 FMA chains (KIND 0) and double -> float -> double conversion chains (KIND 1, two conversions)
+template <int KIND>
+__global__ void fp64_chain(float *out, long long *cyc, int iters, double a, double b)
+{
+    const long long c0 = clock64();
+    double r[kChains];
+    for (int i = 0; i < kChains; ++i) r[i] = threadIdx.x * 1e-3 + i + 0.25;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kInner; ++u)
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) {
+                if (KIND == 0) r[i] = fma(r[i], a, b);
+                else r[i] = static_cast<double>(__double2float_rn(r[i]));
+            }
+    }
+    double s = 0.0;
+    for (int i = 0; i < kChains; ++i) s += r[i];
+    if (s == 1234.5) out[0] = 1.f;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - c0;
+}
+
 }  // namespace
 
 int main()
@@ -107,7 +130,7 @@ int main()
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const double ops_per_thread = static_cast<double>(iters) * kInner * kChains;
+    double ops_per_thread = static_cast<double>(iters) * kInner * kChains;
     const double threads_total = static_cast<double>(blocks) * threads;
     long long *cyc_h = new long long[blocks];
     auto run = [&](const char *name, double results_per_op, auto launch) {
@@ -132,6 +155,10 @@ int main()
     run("fmul", 1.0, [&] { scalar_chain<2><<<blocks, threads>>>(out, cyc, iters, 1.0000001f, 1e-6f); });
     run("ffma2_fp32_results", 2.0, [&] { packed_chain<<<blocks, threads>>>(out, cyc, iters, 1.0001f, 1e-6f); });
     run("mufu_rsqrt", 1.0, [&] { mufu_chain<<<blocks, threads>>>(out, cyc, iters); });
+    const int iters64 = iters / 20;  // the FP64 pipes are narrow: fewer trips
+    ops_per_thread = static_cast<double>(iters64) * kInner * kChains;
+    run("dfma", 1.0, [&] { fp64_chain<0><<<blocks, threads>>>(out, cyc, iters64, 1.0000001, 1e-9); });
+    run("f64_f32_f64_conversions", 2.0, [&] { fp64_chain<1><<<blocks, threads>>>(out, cyc, iters64, 0.0, 0.0); });
     const cudaError_t err = cudaGetLastError();
     std::printf("\"sms\": %d, \"status\": \"%s\"}\n", sm, cudaGetErrorString(err));
     delete[] cyc_h;

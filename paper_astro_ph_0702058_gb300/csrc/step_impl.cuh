@@ -53,8 +53,14 @@ __device__ __forceinline__ void correct_row(const State &S, const int64_t i, con
                                             const double *kp_in, const int64_t t_new, const double tick,
                                             const double eta, const int lmin, const int lmax, DevStatus *st)
 {
-    const double dt = static_cast<double>(t_new - S.t[i]) * tick;
-    const double idt = 1.0 / dt;
+    const int64_t steps = t_new - S.t[i];
+    const double dt = static_cast<double>(steps) * tick;
+    // 1/dt: when the step is 2^k ticks of 2^-lmax (every particle of a block) it
+    // is 2^(lmax - k), built from its exponent bits; otherwise an IEEE division.
+    // Both give the same bits.
+    const double idt = (steps > 0 && (steps & (steps - 1)) == 0)
+                           ? __longlong_as_double(static_cast<long long>(1023 + lmax - (__ffsll(steps) - 1)) << 52)
+                           : 1.0 / dt;
     const double idt2 = idt * idt;
     const double dt3 = dt * dt * dt;
     const double dt4 = dt3 * dt;
@@ -71,8 +77,10 @@ __device__ __forceinline__ void correct_row(const State &S, const int64_t i, con
         const double da = a - ap[c];  // Delta a = a - a_p
         const double a2 = -6.0 * da * idt2 - (4.0 * k + 2.0 * kp[c]) * idt;
         a3[c] = 12.0 * da * idt2 * idt + 6.0 * (k + kp[c]) * idt2;
-        const double xn = xp + dt4 * (a2 / 24.0 + a3[c] * dt / 120.0);
-        const double vn = vp + dt3 * (a2 / 6.0 + a3[c] * dt / 24.0);
+        // the Taylor coefficients 1/24, 1/120, 1/6 as products (an FP64 division
+        // is a long dependent sequence on this part's narrow FP64 pipe)
+        const double xn = xp + dt4 * (a2 * (1.0 / 24.0) + a3[c] * dt * (1.0 / 120.0));
+        const double vn = vp + dt3 * (a2 * (1.0 / 6.0) + a3[c] * dt * (1.0 / 24.0));
         a2e[c] = a2 + a3[c] * dt;  // a^(2) at the end of the step
         finite = finite && isfinite(xn) && isfinite(vn) && isfinite(ap[c]) && isfinite(kp[c]);
         S.x[c][i] = xn;

@@ -131,7 +131,8 @@ def test_every_call_rejects_a_null_handle_without_gpu(libpath):
     names = ["nbody_next_block", "nbody_predict", "nbody_force", "nbody_correct", "nbody_step", "nbody_sync",
              "nbody_energy", "nbody_energy_ds", "nbody_get_state", "nbody_set_state", "nbody_get_predicted", "nbody_get_stats",
              "nbody_ens_init", "nbody_ens_set_shape", "nbody_ens_tune", "nbody_ens_step", "nbody_ens_run",
-             "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_diff_rollout",
+             "nbody_ens_energy", "nbody_ens_get_state", "nbody_ens_get_stats", "nbody_diff_rollout", "nbody_rollout",
+             "nbody_rollout_vjp",
              "nbody_force_noalloc"]
     for name in names:
         fn = getattr(L, name)
