@@ -102,6 +102,10 @@ typedef struct {
                          64): threads per block (64, 128, 256, or 512 with i_block 1)     */
     int j_split;      /* force tuning, 0 = automatic (about 12 waves of blocks): number of
                          j-ranges (>= 1); the double-single mode always takes 128 x 1     */
+    int j_sub;        /* force tuning, plain and compensated modes: 0 = automatic (4 for
+                         blocks of 512 to 8191 rows when j_tile and i_block are 0, else 1);
+                         1 = one thread per row; 4 = 256 threads as 64 rows x 4 threads,
+                         each taking a quarter of every j-tile (j_tile, i_block ignored)    */
     void *stream;     /* cudaStream_t for all work of the context, or NULL                  */
 } nbody_params;
 
@@ -231,6 +235,7 @@ typedef struct {
     int mode;
     int64_t graph_blocks;  /* block steps nbody_step ran inside a replayed CUDA graph */
     int64_t loop_blocks;   /* of those, the ones the device-side loop added (no host round trip) */
+    int last_j_sub;        /* threads per row of the last force kernel (1 or 4)    */
 } nbody_stats;
 
 int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);

@@ -24,7 +24,7 @@ MODES = {"plain": NBODY_MODE_PLAIN, "comp": NBODY_MODE_COMP, "sumcheck": NBODY_M
          "sorted": NBODY_MODE_SORTED, "ds": NBODY_MODE_DS}
 
 _STATE_KEYS = ("x", "v", "a", "k", "t_tick", "level")
-_PARAM_KEYS = ("eta", "eta_init", "lmin", "lmax", "mode", "strict", "i_block", "j_tile", "j_split")
+_PARAM_KEYS = ("eta", "eta_init", "lmin", "lmax", "mode", "strict", "i_block", "j_tile", "j_split", "j_sub")
 
 
 def write_checkpoint(path, m, eps2, params, state) -> None:
@@ -80,14 +80,14 @@ class Simulation:
     """
 
     def __init__(self, m, x, v, eps2, *, eta=0.01, eta_init=None, lmin=6, lmax=26, mode="plain",
-                 strict=False, i_block=0, j_tile=0, j_split=0, stream=None):
+                 strict=False, i_block=0, j_tile=0, j_split=0, j_sub=0, stream=None):
         p = nbody_default_params()
         p.eta = float(eta)
         p.eta_init = float(eta_init) if eta_init is not None else 0.0
         p.lmin, p.lmax = int(lmin), int(lmax)
         p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
         p.strict = 1 if strict else 0
-        p.i_block, p.j_tile, p.j_split = int(i_block), int(j_tile), int(j_split)
+        p.i_block, p.j_tile, p.j_split, p.j_sub = int(i_block), int(j_tile), int(j_split), int(j_sub)
         if stream is not None:
             p.stream = int(getattr(stream, "cuda_stream", stream))
         self.n = int(m.shape[0])
@@ -97,7 +97,8 @@ class Simulation:
         self.eps2 = float(eps2)
         self._m = m.detach().clone() if hasattr(m, "detach") else m.copy()  # fixed masses, for checkpoints
         self._params = {"eta": p.eta, "eta_init": p.eta_init, "lmin": p.lmin, "lmax": p.lmax, "mode": p.mode,
-                        "strict": bool(p.strict), "i_block": p.i_block, "j_tile": p.j_tile, "j_split": p.j_split}
+                        "strict": bool(p.strict), "i_block": p.i_block, "j_tile": p.j_tile, "j_split": p.j_split,
+                        "j_sub": p.j_sub}
         self._ctx = nbody_init(self.n, m, x, v, eps2, p)
 
     @property

@@ -48,7 +48,7 @@ EXPORTS = ("nbody_default_params", "nbody_init", "nbody_next_block", "nbody_pred
 class nbody_params(C.Structure):
     _fields_ = [("eta", C.c_double), ("eta_init", C.c_double), ("lmin", C.c_int), ("lmax", C.c_int),
                 ("mode", C.c_int), ("strict", C.c_int), ("i_block", C.c_int), ("j_tile", C.c_int),
-                ("j_split", C.c_int), ("stream", C.c_void_p)]
+                ("j_split", C.c_int), ("j_sub", C.c_int), ("stream", C.c_void_p)]
 
 
 class nbody_stats(C.Structure):
@@ -56,7 +56,7 @@ class nbody_stats(C.Structure):
                 ("nonfinite", C.c_int64), ("force_calls", C.c_int64), ("pairs", C.c_int64),
                 ("kernel_launches", C.c_int64), ("last_threads", C.c_int), ("last_i_per_thread", C.c_int),
                 ("last_j_split", C.c_int), ("mode", C.c_int), ("graph_blocks", C.c_int64),
-                ("loop_blocks", C.c_int64)]
+                ("loop_blocks", C.c_int64), ("last_j_sub", C.c_int)]
 
 
 class NBodyError(RuntimeError):

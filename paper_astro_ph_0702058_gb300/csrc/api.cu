@@ -127,6 +127,7 @@ struct nbody_ctx {
     StepLoop *loop_host = nullptr;
     bool pred_valid = false;
     int64_t force_n_act = -1;
+    int fused_split = 0;  // > 1: the last force left its j-range partials for the corrector
     nbody_stats stats{};
 };
 
@@ -173,6 +174,9 @@ int absorb_status(nbody_ctx *c)
     if (!f) return NBODY_OK;
     cudaMemsetAsync(&c->st->flags, 0, sizeof(unsigned), c->s);
     c->st_host->flags = 0;
+    if (f & kFlagDebugBounds)
+        return fail(NBODY_ECUDA, "debug build: a device-side index check failed at site %d (access skipped)",
+                    h.debug_site);
     if (f & kFlagTimeout) return fail(NBODY_ETIMEOUT, "a device-side wait for a j-tile gave up (bounded wait)");
     if (f & kFlagBadIndex)
         return fail(NBODY_EINVAL, "active list row %d holds an index outside [0, %lld)", h.bad_index,
@@ -209,26 +213,31 @@ int ensure_partials(nbody_ctx *c, size_t bytes)
     return NBODY_OK;
 }
 
-// Force on a device list already in act_force.
-int force_internal(nbody_ctx *c, int64_t n_act)
+// Force on a device list already in act_force.  With for_step, a shape whose
+// partials the corrector adds (force_partials_fused) skips the reduction;
+// fused_split then tells correct_internal to read them.
+int force_internal(nbody_ctx *c, int64_t n_act, bool for_step = false)
 {
     ForceConfig cfg{};
     const int r = force_choose(c->p.mode, n_act, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
-                               &cfg);
+                               &cfg, c->p.j_sub);
     if (r != NBODY_OK) return fail(r, "unsupported force shape: %d threads x %d i per thread", c->p.j_tile, c->p.i_block);
     const int rp = ensure_partials(c, force_partial_bytes(c->p.mode, cfg, n_act));
     if (rp != NBODY_OK) return rp;
     int64_t launches = 0;
+    const bool fused = for_step && force_partials_fused(c->p.mode, cfg);
     NB_CUDA(force_launch(c->p.mode, c->J, c->n, c->act_force, n_act, c->eps2, cfg,
-                         c->f_acc, c->f_jerk, c->f_pot, c->partials, c->st, c->s, &launches),
+                         c->f_acc, c->f_jerk, c->f_pot, c->partials, c->st, c->s, &launches, nullptr, !fused),
             "force kernel launch");
+    c->fused_split = fused ? cfg.split : 0;
     c->stats.kernel_launches += launches;
     c->stats.force_calls += 1;
     c->stats.pairs += n_act * (c->n - 1);
     c->stats.last_threads = cfg.threads;
     c->stats.last_i_per_thread = cfg.ipt;
     c->stats.last_j_split = cfg.split;
-    c->force_n_act = n_act;
+    c->stats.last_j_sub = cfg.jsub;
+    c->force_n_act = fused ? -1 : n_act;  // a fused force left no rows for nbody_correct to reuse
     return NBODY_OK;
 }
 
@@ -246,10 +255,13 @@ int predict_internal(nbody_ctx *c, int64_t tick)
 }
 
 int correct_internal(nbody_ctx *c, const int32_t *act_dev, int64_t n_act, const double *acc_dev,
-                     const double *jerk_dev)
+                     const double *jerk_dev, bool fused_partials = false)
 {
+    const int split = fused_partials ? c->fused_split : 0;
     NB_CUDA(correct_launch(c->S, act_dev, n_act, acc_dev, jerk_dev, c->t_pred, c->p.eta, c->p.lmin, c->p.lmax,
-                           c->st, c->s, &c->stats.kernel_launches),
+                           c->st, c->s, &c->stats.kernel_launches, nullptr,
+                           split > 1 ? static_cast<const float *>(c->partials) : nullptr, split,
+                           two_word_sums(c->p.mode)),
             "corrector launch");
     if (n_act > 0) {
         c->t_max = std::max(c->t_max, c->t_pred);
@@ -288,6 +300,7 @@ int check_params(const nbody_params *p)
     if (p->i_block != 0 && p->i_block != 1 && p->i_block != 2 && p->i_block != 4)
         return fail(NBODY_EINVAL, "i_block must be 0, 1, 2 or 4");
     if (p->j_split < 0) return fail(NBODY_EINVAL, "j_split must be >= 0");
+    if (p->j_sub != 0 && p->j_sub != 1 && p->j_sub != 4) return fail(NBODY_EINVAL, "j_sub must be 0, 1 or 4");
     return NBODY_OK;
 }
 
@@ -333,6 +346,7 @@ int rollout_impl(const char *who, int64_t n, const double *m, const double *x0, 
     nbody_ctx *c = nullptr;
     int r = nbody_init(&c, n, m, x0, v0, eps2, &p);
     if (r != NBODY_OK) return r;
+    c->J.aos = true;  // the force's vector-Jacobian product reads the float4 j-stream
     const size_t nd = static_cast<size_t>(n);
     const size_t npad = static_cast<size_t>(c->n_pad);
     const int64_t n_ck = steps / checkpoint_every + 1;
@@ -589,6 +603,7 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     c->J.vello = c->jbuf + 3 * c->n_pad;
     c->J.soa = reinterpret_cast<float *>(c->jbuf + 4 * c->n_pad);
     c->J.n_pad = c->n_pad;
+    c->J.aos = force_needs_aos(prm.mode);
 
     cudaStream_t s = c->s;
     int64_t *L = &c->stats.kernel_launches;
@@ -602,6 +617,7 @@ int nbody_init(nbody_ctx **out, int64_t n, const double *m, const double *x, con
     NB_INIT(aos_to_soa_launch(c->stage, S.x[0], S.x[1], S.x[2], n, s, L), "layout kernel");
     NB_INIT(to_device(c->stage + 3 * nd, v, 3 * nd * sizeof(double), s), "velocity upload");
     NB_INIT(aos_to_soa_launch(c->stage + 3 * nd, S.v[0], S.v[1], S.v[2], n, s, L), "layout kernel");
+    NB_INIT(mass_jstream_launch(S, c->J, s, L), "mass kernel");
 
     // t = 0: predicted state = state; full force; first levels.
     r = predict_internal(c, 0);
@@ -707,17 +723,21 @@ int nbody_correct(nbody_ctx *c, const int32_t *active, int64_t n_act, const doub
 namespace {
 
 // Rows the small-block graph is sized for: its force grid (rows / 64 x j-ranges)
-// stays near 2048 blocks, so blocks beyond the actual size exit at little cost.
+// stays near 2048 blocks, so blocks beyond the actual size exit at little cost,
+// and below the rows where the automatic shape turns to j-subgroups, so that all
+// the small blocks share the graph's shape.
 int64_t graph_rows_for(const nbody_ctx *c)
 {
     const int64_t n_tiles = c->n_pad / kJTile;
     const int64_t by_grid = 64 * std::max<int64_t>(1, 2048 / n_tiles);
-    return std::min<int64_t>({c->n, by_grid, 8191});
+    const int64_t cap = n_tiles >= kJSubMinTiles ? kJSubMinRows - 1 : 8191;
+    return std::min<int64_t>({c->n, by_grid, cap});
 }
 
 bool same_shape(const ForceConfig &a, const ForceConfig &b)
 {
-    return a.threads == b.threads && a.ipt == b.ipt && a.split == b.split && a.tiles_per_split == b.tiles_per_split;
+    return a.threads == b.threads && a.ipt == b.ipt && a.jsub == b.jsub && a.split == b.split &&
+           a.tiles_per_split == b.tiles_per_split;
 }
 
 // One block step sized for graph_rows rows, captured on cs: predictor, force,
@@ -728,12 +748,14 @@ cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches,
     const int64_t rows = c->graph_rows;
     cudaError_t e = predict_launch(c->S, c->J, 0, c->p.lmax, predict_lo_parts(c->p.mode), cs, launches,
                                    &c->sched_out->t_blk);
+    const bool fused = force_partials_fused(c->p.mode, c->graph_cfg);
     if (e == cudaSuccess)
         e = force_launch(c->p.mode, c->J, c->n, c->act_sched, rows, c->eps2, c->graph_cfg, c->f_acc, c->f_jerk,
-                         c->f_pot, c->partials, c->st, cs, launches, &c->sched_out->n_act);
+                         c->f_pot, c->partials, c->st, cs, launches, &c->sched_out->n_act, !fused);
     if (e == cudaSuccess)
         e = correct_launch(c->S, c->act_sched, rows, c->f_acc, c->f_jerk, 0, c->p.eta, c->p.lmin, c->p.lmax, c->st,
-                           cs, launches, c->sched_out);
+                           cs, launches, c->sched_out, fused ? static_cast<const float *>(c->partials) : nullptr,
+                           fused ? c->graph_cfg.split : 0, two_word_sums(c->p.mode));
     if (e == cudaSuccess)
         e = la ? schedule_loop_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, *la, cs, launches)
                : schedule_launch(c->S, c->p.lmax, c->act_sched, c->sched_out, c->sched_scratch, cs, launches);
@@ -744,7 +766,7 @@ cudaError_t capture_block_step(nbody_ctx *c, cudaStream_t cs, int64_t *launches,
 // clamp in strict mode (the flags the host would report after that block).
 unsigned loop_stop_flags(const nbody_ctx *c)
 {
-    return kFlagTimeout | kFlagBadIndex | kFlagNonfinite | (c->p.strict ? kFlagDtMin : 0u);
+    return kFlagTimeout | kFlagBadIndex | kFlagNonfinite | kFlagDebugBounds | (c->p.strict ? kFlagDtMin : 0u);
 }
 
 // Builds the replayed graph: the block step as the body of a while-node, whose
@@ -813,7 +835,7 @@ int set_graph_fits(nbody_ctx *c)
     for (int64_t na = 1; na < len; ++na) {
         ForceConfig cfg{};
         fits[na] = force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
-                                &cfg) == NBODY_OK && same_shape(cfg, c->graph_cfg);
+                                &cfg, c->p.j_sub) == NBODY_OK && same_shape(cfg, c->graph_cfg);
     }
     NB_CUDA(dev_alloc(reinterpret_cast<void **>(&c->graph_fits), static_cast<size_t>(len)), "graph table allocation");
     NB_CUDA(cudaMemcpy(c->graph_fits, fits.data(), static_cast<size_t>(len), cudaMemcpyHostToDevice),
@@ -880,7 +902,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     if (g_step_graphs > 0 && packed && c->graph_rows == 0) {
         c->graph_rows = graph_rows_for(c);
         if (force_choose(c->p.mode, c->graph_rows, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block, c->p.j_split,
-                         &c->graph_cfg) != NBODY_OK)
+                         &c->graph_cfg, c->p.j_sub) != NBODY_OK)
             c->graph_rows = -1;
     }
     int64_t tb = 0, na = 0;
@@ -889,7 +911,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
         ForceConfig cfg{};
         bool use_graph = g_step_graphs > 0 && packed && c->graph_rows > 0 && na <= c->graph_rows &&
                          force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block,
-                                      c->p.j_split, &cfg) == NBODY_OK &&
+                                      c->p.j_split, &cfg, c->p.j_sub) == NBODY_OK &&
                          same_shape(cfg, c->graph_cfg);
         if (use_graph) {
             r = build_step_graph(c);
@@ -919,6 +941,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
             c->stats.last_threads = cfg.threads;
             c->stats.last_i_per_thread = cfg.ipt;
             c->stats.last_j_split = cfg.split;
+            c->stats.last_j_sub = cfg.jsub;
             c->t_max = std::max(c->t_max, last_t);
             c->t_pred = last_t;
             c->pred_valid = false;
@@ -935,9 +958,9 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
         NB_CUDA(cudaMemcpyAsync(c->act_force, c->act_sched, static_cast<size_t>(na) * sizeof(int32_t),
                                 cudaMemcpyDeviceToDevice, c->s),
                 "list copy");
-        r = force_internal(c, na);
+        r = force_internal(c, na, true);
         if (r != NBODY_OK) break;
-        r = correct_internal(c, c->act_sched, na, c->f_acc, c->f_jerk);
+        r = correct_internal(c, c->act_sched, na, c->f_acc, c->f_jerk, true);
         if (r != NBODY_OK) break;
         ++done;
         r = schedule_internal(c, &tb, &na);
@@ -1023,6 +1046,8 @@ int nbody_get_predicted(nbody_ctx *c, float *posm, float *vel, float *poslo)
     if (!c) return fail(NBODY_EINVAL, "nbody_get_predicted: null context");
     if (!c->pred_valid) return fail(NBODY_ESTATE, "nbody_get_predicted: no current prediction");
     const size_t bytes = static_cast<size_t>(c->n) * sizeof(float4);
+    if (!c->J.aos && (posm || vel || poslo))  // this context's predictor writes the SoA stream only
+        NB_CUDA(aos_from_soa_launch(c->J, c->n, c->s, &c->stats.kernel_launches), "layout kernel");
     if (posm) NB_CUDA(cudaMemcpyAsync(posm, c->J.posm, bytes, cudaMemcpyDefault, c->s), "j-stream copy");
     if (vel) NB_CUDA(cudaMemcpyAsync(vel, c->J.vel, bytes, cudaMemcpyDefault, c->s), "j-stream copy");
     if (poslo) NB_CUDA(cudaMemcpyAsync(poslo, c->J.poslo, bytes, cudaMemcpyDefault, c->s), "j-stream copy");

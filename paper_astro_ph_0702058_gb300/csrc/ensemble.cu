@@ -188,7 +188,8 @@ __global__ void ens_predict_kernel(const EnsDev E, double tick, int comp)
         const double dt = static_cast<double>(E.t_blk[c] - E.S.t[i]) * tick;
         double xp[3], vp[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) predict_dim(E.S.x[q][i], E.S.v[q][i], E.S.a[q][i], E.S.k[q][i], dt, xp[q], vp[q]);
+        const PredDt pd = pred_dt(dt);
+        for (int q = 0; q < 3; ++q) predict_dim(E.S.x[q][i], E.S.v[q][i], E.S.a[q][i], E.S.k[q][i], pd, xp[q], vp[q]);
         const int64_t j = E.joff[c] + (i - E.off[c]);
         const float hx = __double2float_rn(xp[0]), hy = __double2float_rn(xp[1]), hz = __double2float_rn(xp[2]);
         const float hm = __double2float_rn(E.S.m[i]);

@@ -21,6 +21,11 @@ cudaError_t reduce_check(const float *part, int split, int n_act, double *acc, d
 
 int g_skip_first_copy = 0;  // test hook (nbody_debug_skip_tile_copy)
 
+bool force_needs_aos(int mode)
+{
+    return !NB_PACKED || mode == kModeDS || mode == kModeSorted;
+}
+
 bool force_reads_device_rows(int mode)
 {
     return NB_PACKED && (mode == kModePlain || mode == kModeComp);
@@ -30,6 +35,7 @@ namespace {
 
 int shape_index(int threads, int ipt)
 {
+    if (ipt < 0) return threads == kJSubThreads ? 10 : -1;  // the j-subgroup shape
     if (threads == 512) return ipt == 1 ? 9 : -1;  // one i per thread only
     const int ti = threads == 64 ? 0 : threads == 128 ? 1 : threads == 256 ? 2 : -1;
     const int ii = ipt == 1 ? 0 : ipt == 2 ? 1 : ipt == 4 ? 2 : -1;
@@ -40,8 +46,8 @@ int shape_index(int threads, int ipt)
 // every device this library runs on is the same sm_103 part).
 int occupancy(int mode, int threads, int ipt)
 {
-    static int cache[5][10];
-    static bool filled[5][10];
+    static int cache[5][11];
+    static bool filled[5][11];
     const int si = shape_index(threads, ipt);
     if (si < 0 || mode < 0 || mode > 4) return 0;
     if (!filled[mode][si]) {
@@ -58,11 +64,25 @@ int occupancy(int mode, int threads, int ipt)
 }  // namespace
 
 int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_threads, int req_ipt,
-                 int req_split, ForceConfig *cfg)
+                 int req_split, ForceConfig *cfg, int req_jsub)
 {
     const int n_tiles = static_cast<int>(n_pad / kJTile);
     int threads = req_threads;
     int ipt = req_ipt;
+    // j-subgroups: blocks of kJSubMinRows to 8191 rows in the packed plain and compensated
+    // modes take 256 threads as 64 rows x 4 subgroups, unless the caller fixes a shape
+    // (for streams of kJSubMinTiles tiles or more: at small n a block is all latency).
+    // Smaller blocks keep 64 threads, one per row: their time is one range's latency, and
+    // one shape for all of them lets the block-step graph take them all.
+    const bool jsub_ok = NB_PACKED && (mode == kModePlain || mode == kModeComp);
+    const bool jsub = jsub_ok && (req_jsub == kJSub || (req_jsub == 0 && req_threads == 0 && req_ipt == 0 &&
+                                                        n_act >= kJSubMinRows && n_act < 8192 &&
+                                                        n_tiles >= kJSubMinTiles));
+    if (req_jsub > 1 && (!jsub_ok || req_jsub != kJSub)) return NBODY_EINVAL;
+    if (jsub) {
+        threads = kJSubThreads;
+        ipt = -1;  // the occupancy / shape key of the j-subgroup instance
+    }
     // Packed loop: one i per thread keeps registers low (74 plain, 94
     // compensated) and resident warps high, which beats amortising the shared
     // loads over 2 or 4 i (134-252 registers).  At N = 2^20, in Tpairs/s:
@@ -76,7 +96,7 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     if (threads == 0) threads = n_act >= 8192 ? 256 : 64;
     if (ipt == 0) ipt = 1;
     if (shape_index(threads, ipt) < 0) return NBODY_EINVAL;
-    const int per = threads * ipt;
+    const int per = jsub ? kJSubThreads / kJSub : threads * ipt;  // rows of a block
     const int n_iblk = static_cast<int>(std::max<int64_t>(1, (n_act + per - 1) / per));
     int split = req_split;
     if (split <= 0) {
@@ -115,10 +135,23 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
         if (n_tiles >= 2 && static_cast<int64_t>(n_iblk) * (n_tiles / 2) >= slots)
             split = std::min(split, n_tiles / 2);
     }
+    if (req_split <= 0 && jsub) {
+        // j-subgroup blocks are short: give each range 8, 4 or 2 tiles while the grid
+        // still fills the GPU (8 only with six waves or more).  At N = 65536: 1024 and
+        // 1594 rows fastest with 4 tiles (compensated 117 and 164 us, against 125 and 184
+        // with 2), 4096 rows with 8.
+        const int64_t slots = static_cast<int64_t>(sm_count) * std::max(1, occupancy(mode, threads, ipt));
+        int t = 1;
+        if (n_tiles >= 8 && static_cast<int64_t>(n_iblk) * (n_tiles / 8) >= 6 * slots) t = 8;
+        else if (n_tiles >= 4 && static_cast<int64_t>(n_iblk) * (n_tiles / 4) >= slots) t = 4;
+        else if (n_tiles >= 2 && static_cast<int64_t>(n_iblk) * (n_tiles / 2) >= slots) t = 2;
+        split = (n_tiles + t - 1) / t;
+    }
     const int tps = (n_tiles + split - 1) / split;
     split = (n_tiles + tps - 1) / tps;
     cfg->threads = threads;
-    cfg->ipt = ipt;
+    cfg->ipt = jsub ? 1 : ipt;
+    cfg->jsub = jsub ? kJSub : 1;
     cfg->split = split;
     cfg->tiles_per_split = tps;
     cfg->n_iblk = n_iblk;
@@ -132,9 +165,14 @@ size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act)
     return static_cast<size_t>(cfg.split) * nc * static_cast<size_t>(n_act) * sizeof(float);
 }
 
+bool force_partials_fused(int mode, const ForceConfig &cfg)
+{
+    return force_reads_device_rows(mode) && cfg.split > 1 && cfg.split < kFusedSplitMax;
+}
+
 cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active, int64_t n_act, double eps2_d,
                          const ForceConfig &cfg, double *acc, double *jerk, double *pot, void *partials,
-                         DevStatus *st, cudaStream_t s, int64_t *launches, const long long *n_act_dev)
+                         DevStatus *st, cudaStream_t s, int64_t *launches, const long long *n_act_dev, bool reduce)
 {
     if (n_act <= 0) return cudaSuccess;
     const float eps2 = static_cast<float>(eps2_d);
@@ -180,7 +218,7 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
                                          : force_dispatch_plain(P, c, s);
     if (e != cudaSuccess) return e;
     ++*launches;
-    if (c.split > 1) {
+    if (c.split > 1 && reduce) {
         e = mode == kModeComp    ? reduce_comp(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev)
             : mode == kModeCheck ? reduce_check(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev)
                                  : reduce_plain(P.part, c.split, P.n_act, acc, jerk, pot, s, n_act_dev);

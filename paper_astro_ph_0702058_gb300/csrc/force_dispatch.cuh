@@ -19,6 +19,30 @@ constexpr bool aos_packed_shape()
     return IPT == 1 && (NT == 64 || NT == 256);
 }
 
+// The j-subgroup instance (plain and compensated modes, SoA j-stream).
+template <int MODE>
+cudaError_t launch_force_jsub(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
+{
+    if constexpr (NB_PACKED && (MODE == kModePlain || MODE == kModeComp)) {
+        if (P.soa) {
+            force_kernel_x2<MODE, kJSubThreads, 1, FoldLen<MODE>::value, true, kJSub>
+                <<<dim3(cfg.n_iblk, cfg.split), kJSubThreads, 0, s>>>(P);
+            return cudaGetLastError();
+        }
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
+template <int MODE>
+int occupancy_jsub()
+{
+    int b = 0;
+    if constexpr (NB_PACKED && (MODE == kModePlain || MODE == kModeComp))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, force_kernel_x2<MODE, kJSubThreads, 1, FoldLen<MODE>::value, true, kJSub>, kJSubThreads, 0);
+    return b;
+}
+
 template <int MODE, int NT, int IPT>
 cudaError_t launch_force_instance(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
 {
@@ -53,6 +77,7 @@ int occupancy_instance(int *blocks)
 template <int MODE>
 cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
 {
+    if (cfg.jsub > 1) return launch_force_jsub<MODE>(P, cfg, s);
 #define NB_CASE(T, I) \
     if (cfg.threads == T && cfg.ipt == I) return launch_force_instance<MODE, T, I>(P, cfg, s);
     NB_CASE(64, 1)
@@ -72,6 +97,7 @@ cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStr
 template <int MODE>
 int force_occupancy(int threads, int ipt)
 {
+    if (ipt < 0) return occupancy_jsub<MODE>();  // ipt < 0 asks for the j-subgroup shape
     int b = 0;
 #define NB_CASE(T, I) \
     if (threads == T && ipt == I) { occupancy_instance<MODE, T, I>(&b); return b; }

@@ -235,13 +235,16 @@ __device__ __forceinline__ void tile_sums_x2_check(const SoaTile<kModeCheck> &T,
     }
 }
 
-template <int MODE, int IPT, int PF, bool SELF>
+// Sums over the j of one staged tile (starting at global index j0), or over
+// the JL of them from jstart on (a j-subgroup's share of the tile).
+template <int MODE, int IPT, int PF, bool SELF, int JL = kJTile>
 __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j0, const I2 (&I)[IPT],
                                              const int (&gi)[IPT], const f2_t E2, const f2_t NEG3,
-                                             float (&tot)[IPT][7], float (&lo)[IPT][7])
+                                             float (&tot)[IPT][7], float (&lo)[IPT][7], const int jstart = 0)
 {
+    static_assert(JL % PF == 0 || PF % JL == 0, "fold length and j share");
 #pragma unroll 1
-    for (int jb = 0; jb < kJTile; jb += PF) {
+    for (int jb = jstart; jb < jstart + JL; jb += (PF < JL ? PF : JL)) {
         f2_t p[IPT][7];
 #pragma unroll
         for (int u = 0; u < IPT; ++u)
@@ -250,7 +253,7 @@ __device__ __forceinline__ void tile_sums_x2(const SoaTile<MODE> &T, const int j
         constexpr int JS = NB_X2_JSTEP;
         static_assert(JS == 2 || JS == 4, "j group of 2 or 4");
 NB_UNROLL(NB_X2_UNROLL)
-        for (int jj = 0; jj < PF; jj += JS) {
+        for (int jj = 0; jj < (PF < JL ? PF : JL); jj += JS) {
             f2_t v[SoaTile<MODE>::NA][JS / 2];
 #pragma unroll
             for (int a = 0; a < SoaTile<MODE>::NA; ++a) {
@@ -293,12 +296,21 @@ NB_UNROLL(NB_X2_UNROLL)
 #define NB_X2_BOUNDS(NT) __launch_bounds__(NT)
 #endif
 
-template <int MODE, int NT, int IPT, int PF, bool SOAIN>
+template <int MODE, int NT, int IPT, int PF, bool SOAIN, int JSUB = 1>
 __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
 {
     // SOAIN: the tiles come straight from the SoA j-stream into the SoA tile
     // buffers (one bulk copy per array, one barrier per tile); otherwise the
     // float4 stream is staged and transposed (two barriers per tile).
+    // JSUB > 1: a block holds NT / JSUB rows, each with JSUB threads that take
+    // consecutive quarters (JSUB = 4) of every tile; at the end the JSUB sums of a
+    // row are added in shared memory in subgroup order (FP64).  The same rows
+    // per block as JSUB = 1 with NT / JSUB threads, but blocks JSUB times shorter:
+    // more, evenly filled waves for mid-size blocks, and each tile copy serves
+    // JSUB times the pairs.
+    static_assert(JSUB == 1 || (IPT == 1 && SOAIN && NT % (32 * JSUB) == 0), "j-subgroups: one row per thread");
+    constexpr int RB = NT / JSUB;          // rows of a block (per i of a thread)
+    constexpr int JL = kJTile / JSUB;      // j of a tile per subgroup
     constexpr int NARR = is_ds(MODE) ? 3 : 2;
     constexpr int NA = SoaTile<MODE>::NA;
     constexpr uint32_t kTileBytes = kJTile * sizeof(float4);
@@ -311,8 +323,9 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     __shared__ __align__(8) uint64_t bar[2];
 
     const int n_act = P.n_act_dev ? static_cast<int>(*P.n_act_dev) : P.n_act;
-    if (static_cast<int>(blockIdx.x) * NT * IPT >= n_act) return;  // a launch sized for more rows
+    if (static_cast<int>(blockIdx.x) * RB * IPT >= n_act) return;  // a launch sized for more rows
     const int tid = threadIdx.x;
+    const int row = tid % RB, sub = tid / RB;
     const int t_begin = blockIdx.y * P.tiles_per_split;
     const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
     const f2_t E2 = f2_pack(P.eps2, P.eps2);
@@ -323,7 +336,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     int gi[IPT];
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
-        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        const int q = (blockIdx.x * IPT + u) * RB + row;
         int idx = -1;
         if (q < n_act) {
             idx = P.active[q];
@@ -335,7 +348,17 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         }
         gi[u] = idx;
         const int l = idx >= 0 ? idx : 0;
-        const float4 xp = P.posm[l], vp = P.vel[l];
+        float4 xp, vp, lp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (SOAIN) {  // the rows from the structure-of-arrays stream, as the tiles
+            const float *a = P.soa + l;
+            xp = make_float4(a[0], a[n_pad], a[2 * n_pad], 0.f);
+            vp = make_float4(a[4 * n_pad], a[5 * n_pad], a[6 * n_pad], 0.f);
+            if (is_ds(MODE)) lp = make_float4(a[7 * n_pad], a[8 * n_pad], a[9 * n_pad], 0.f);
+        } else {
+            xp = P.posm[l];
+            vp = P.vel[l];
+            if (is_ds(MODE)) lp = P.poslo[l];
+        }
         I[u].x = f2_pack(xp.x, xp.x);
         I[u].y = f2_pack(xp.y, xp.y);
         I[u].z = f2_pack(xp.z, xp.z);
@@ -343,7 +366,6 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         I[u].vy = f2_pack(vp.y, vp.y);
         I[u].vz = f2_pack(vp.z, vp.z);
         if (is_ds(MODE)) {
-            const float4 lp = P.poslo[l];
             I[u].lx = f2_pack(lp.x, lp.x);
             I[u].ly = f2_pack(lp.y, lp.y);
             I[u].lz = f2_pack(lp.z, lp.z);
@@ -374,6 +396,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         const size_t off = static_cast<size_t>(t0) * kJTile;
         if constexpr (SOAIN) {
             const int nt = min(TG, t_end - t0);
+            if (!NB_CHECK(static_cast<size_t>(t0 + nt) * kJTile <= n_pad, P.st, 1)) return;  // no copy, the wait gives up
             mbar_arrive_expect_tx(&bar[b], nt * NA * kArrBytes);
             for (int k = 0; k < nt; ++k)
 #pragma unroll
@@ -430,8 +453,13 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             bool self_tile = false;
 #pragma unroll
             for (int u = 0; u < IPT; ++u)
-                self_tile |= static_cast<unsigned>(gi[u] - j0) < static_cast<unsigned>(kJTile);
-            if constexpr (MODE == kModeCheck) {
+                self_tile |= static_cast<unsigned>(gi[u] - j0 - sub * JL) < static_cast<unsigned>(JL);
+            if constexpr (JSUB > 1) {
+                if (self_tile)
+                    tile_sums_x2<MODE, IPT, PF, true, JL>(T, j0, I, gi, E2, NEG3, tot, lo, sub * JL);
+                else
+                    tile_sums_x2<MODE, IPT, PF, false, JL>(T, j0, I, gi, E2, NEG3, tot, lo, sub * JL);
+            } else if constexpr (MODE == kModeCheck) {
                 if (self_tile)
                     tile_sums_x2_check<IPT, true>(T, j0, I, gi, E2, NEG3, P.opaque_zero, ph, pl);
                 else
@@ -463,6 +491,54 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         return;
     }
 
+    if constexpr (JSUB > 1) {
+        // the JSUB sums of each row, through shared memory (the tile buffers are
+        // free: every copy issued has been waited for), added in subgroup order
+        constexpr int NCS = is_ds(MODE) ? 14 : 7;
+        static_assert(sizeof(soa) >= sizeof(float) * NCS * NT, "combine buffer");
+        float *red = reinterpret_cast<float *>(soa);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            red[(sub * NCS + c) * RB + row] = tot[0][c];
+            if (is_ds(MODE)) red[(sub * NCS + 7 + c) * RB + row] = lo[0][c];
+        }
+        __syncthreads();
+        const int q = blockIdx.x * RB + row;
+        if (sub != 0 || q >= n_act) return;
+        double r[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            double t = 0.0;
+#pragma unroll
+            for (int g = 0; g < JSUB; ++g) {
+                t += static_cast<double>(red[(g * NCS + c) * RB + row]);
+                if (is_ds(MODE)) t += static_cast<double>(red[(g * NCS + 7 + c) * RB + row]);
+            }
+            r[c] = t;
+        }
+        if (gridDim.y == 1) {
+            double *pa = P.acc + 3 * static_cast<size_t>(q);
+            double *pk = P.jerk + 3 * static_cast<size_t>(q);
+            pa[0] = r[0];
+            pa[1] = r[1];
+            pa[2] = r[2];
+            pk[0] = r[3];
+            pk[1] = r[4];
+            pk[2] = r[5];
+            P.pot[q] = r[6];
+        } else {  // a partial sum: (hi, lo) of the FP64 value, or its float
+            float *base = P.part + static_cast<size_t>(blockIdx.y) * NCS * n_act + q;
+            if (!NB_CHECK(q < n_act, P.st, 2)) return;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const float h = static_cast<float>(r[c]);
+                base[static_cast<size_t>(c) * n_act] = h;
+                if (is_ds(MODE)) base[static_cast<size_t>(7 + c) * n_act] = static_cast<float>(r[c] - static_cast<double>(h));
+            }
+        }
+        return;
+    }
     if constexpr (MODE == kModeCheck) {
         // even and odd sums into one double-single pair: TwoSum of the high
         // words, the low words and the error added (all round to nearest)
@@ -480,7 +556,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     }
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
-        const int q = (blockIdx.x * IPT + u) * NT + tid;
+        const int q = (blockIdx.x * IPT + u) * RB + row;
         if (q >= n_act) continue;
         if (gridDim.y == 1) {
             double r[7];
@@ -500,6 +576,7 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         } else {
             constexpr int NC = is_ds(MODE) ? 14 : 7;
             float *base = P.part + static_cast<size_t>(blockIdx.y) * NC * n_act + q;
+            if (!NB_CHECK(static_cast<int>(blockIdx.y) < static_cast<int>(gridDim.y) && q < n_act, P.st, 2)) continue;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 base[static_cast<size_t>(c) * n_act] = tot[u][c];

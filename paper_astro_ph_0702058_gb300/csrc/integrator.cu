@@ -21,48 +21,86 @@ int blocks_for(int64_t n, int threads, int cap = 1 << 20)
     return static_cast<int>(b < cap ? b : cap);
 }
 
+// Predictor of Sect. 2 for every particle, FP64, and the FP32 j-stream the
+// force reads.  FP64-pipe work per particle: the step, 15 fused multiply-adds
+// and the lo differences; the roundings to float run on the integer pipe
+// (d2f_rn) and the masses' were done once at set-up (mass_jstream_kernel).
+// The structure-of-arrays stream is always written; the float4 streams only
+// when a kernel of this context reads them (J.aos).
+template <bool INTCONV>
+__device__ __forceinline__ float to_f32(const double d)
+{
+    return INTCONV ? d2f_rn(d) : __double2float_rn(d);
+}
+template <bool INTCONV>
+__device__ __forceinline__ double to_f64(const float f)
+{
+    return INTCONV ? f2d(f) : static_cast<double>(f);
+}
+
+// INTCONV: the roundings on the integer pipe (throughput, large n) or by the
+// hardware conversion (latency, small n); both give the same bits.
+template <bool INTCONV>
 __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, double tick, int lo_parts,
                                const long long *t_dev)
 {
     if (t_dev) t_new = *t_dev;
+    const int64_t np = J.n_pad;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const double dt = static_cast<double>(t_new - S.t[i]) * tick;
+        const PredDt pd = pred_dt(static_cast<double>(t_new - S.t[i]) * tick);
         double xp[3], vp[3];
+        float h[3], hv[3], lx[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) predict_dim(S.x[c][i], S.v[c][i], S.a[c][i], S.k[c][i], dt, xp[c], vp[c]);
-        const float hx = __double2float_rn(xp[0]);
-        const float hy = __double2float_rn(xp[1]);
-        const float hz = __double2float_rn(xp[2]);
-        const float hm = __double2float_rn(S.m[i]);
-        const float hvx = __double2float_rn(vp[0]), hvy = __double2float_rn(vp[1]), hvz = __double2float_rn(vp[2]);
-        J.posm[i] = make_float4(hx, hy, hz, hm);
-        J.vel[i] = make_float4(hvx, hvy, hvz, 0.f);
-        if (lo_parts)
-            J.poslo[i] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
-                                     __double2float_rn(xp[1] - static_cast<double>(hy)),
-                                     __double2float_rn(xp[2] - static_cast<double>(hz)),
-                                     lo_parts > 1 ? __double2float_rn(S.m[i] - static_cast<double>(hm)) : 0.f);
-        if (lo_parts > 1)
-            J.vello[i] = make_float4(__double2float_rn(vp[0] - static_cast<double>(hvx)),
-                                     __double2float_rn(vp[1] - static_cast<double>(hvy)),
-                                     __double2float_rn(vp[2] - static_cast<double>(hvz)), 0.f);
-        if (J.soa) {
-            float *a = J.soa + i;
-            const int64_t np = J.n_pad;
-            a[0] = hx;
-            a[np] = hy;
-            a[2 * np] = hz;
-            a[3 * np] = hm;
-            a[4 * np] = hvx;
-            a[5 * np] = hvy;
-            a[6 * np] = hvz;
-            if (lo_parts) {
-                a[7 * np] = __double2float_rn(xp[0] - static_cast<double>(hx));
-                a[8 * np] = __double2float_rn(xp[1] - static_cast<double>(hy));
-                a[9 * np] = __double2float_rn(xp[2] - static_cast<double>(hz));
-            }
+        for (int c = 0; c < 3; ++c) {
+            predict_dim(S.x[c][i], S.v[c][i], S.a[c][i], S.k[c][i], pd, xp[c], vp[c]);
+            h[c] = to_f32<INTCONV>(xp[c]);
+            hv[c] = to_f32<INTCONV>(vp[c]);
+            lx[c] = lo_parts ? to_f32<INTCONV>(xp[c] - to_f64<INTCONV>(h[c])) : 0.f;  // the difference is exact
         }
+        float *a = J.soa + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c * np] = h[c];
+            a[(4 + c) * np] = hv[c];
+            if (lo_parts) a[(7 + c) * np] = lx[c];
+        }
+        if (J.aos) {
+            const float hm = a[3 * np];
+            J.posm[i] = make_float4(h[0], h[1], h[2], hm);
+            J.vel[i] = make_float4(hv[0], hv[1], hv[2], 0.f);
+            if (lo_parts)
+                J.poslo[i] = make_float4(lx[0], lx[1], lx[2],
+                                         lo_parts > 1 ? d2f_rn(S.m[i] - f2d(hm)) : 0.f);
+            if (lo_parts > 1)
+                J.vello[i] = make_float4(d2f_rn(vp[0] - f2d(hv[0])), d2f_rn(vp[1] - f2d(hv[1])),
+                                         d2f_rn(vp[2] - f2d(hv[2])), 0.f);
+        }
+    }
+}
+
+// The masses of the j-stream (structure-of-arrays and float4 forms), once at set-up.
+__global__ void mass_jstream_kernel(const State S, const JStream J)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < S.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float hm = __double2float_rn(S.m[i]);
+        J.soa[3 * J.n_pad + i] = hm;
+        J.posm[i].w = hm;
+    }
+}
+
+// The float4 streams from the structure-of-arrays stream (on demand, for
+// readers of the float4 form when the predictor did not write it).
+__global__ void aos_from_soa_kernel(const JStream J, int64_t n)
+{
+    const int64_t np = J.n_pad;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float *a = J.soa + i;
+        J.posm[i] = make_float4(a[0], a[np], a[2 * np], a[3 * np]);
+        J.vel[i] = make_float4(a[4 * np], a[5 * np], a[6 * np], 0.f);
+        J.poslo[i] = make_float4(a[7 * np], a[8 * np], a[9 * np], 0.f);
     }
 }
 
@@ -70,7 +108,8 @@ __global__ void predict_kernel(const State S, const JStream J, int64_t t_new, do
 __global__ void correct_kernel(const State S, const int32_t *__restrict__ active, int64_t n_act,
                                const double *__restrict__ acc, const double *__restrict__ jerk,
                                int64_t t_new, double tick, double eta, int lmin, int lmax,
-                               DevStatus *st, const SchedOut *sched_dev)
+                               DevStatus *st, const SchedOut *sched_dev, const float *__restrict__ part,
+                               int split, int two_word)
 {
     if (sched_dev) {
         t_new = sched_dev->t_blk;
@@ -82,6 +121,36 @@ __global__ void correct_kernel(const State S, const int32_t *__restrict__ active
     if (i < 0 || i >= S.n) {
         atomicOr(&st->flags, kFlagBadIndex);
         st->bad_index = static_cast<int>(q);
+        return;
+    }
+    if (part) {  // the block's j-range partials, added as reduce_partials_kernel does
+        const int nc = two_word ? 14 : 7;
+        if (!NB_CHECK(split > 1 && split < kFusedSplitMax, st, 3)) return;
+        // all loads first (unrolled over the largest fused split, predicated), so
+        // their latencies overlap; then the sums in ascending range order
+        float hv[kFusedSplitMax - 1][6], lv[kFusedSplitMax - 1][6];
+#pragma unroll
+        for (int sp = 0; sp < kFusedSplitMax - 1; ++sp)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float *b = part + static_cast<size_t>(sp) * nc * n_act + q;
+                hv[sp][c] = sp < split ? b[static_cast<size_t>(c) * n_act] : 0.0f;
+                lv[sp][c] = (sp < split && two_word) ? b[static_cast<size_t>(7 + c) * n_act] : 0.0f;
+            }
+        double f[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int sp = 0; sp < kFusedSplitMax - 1; ++sp) {
+                if (sp < split) {
+                    s += static_cast<double>(hv[sp][c]);
+                    if (two_word) s += static_cast<double>(lv[sp][c]);
+                }
+            }
+            f[c] = s;
+        }
+        correct_row(S, i, f, f + 3, t_new, tick, eta, lmin, lmax, st);
         return;
     }
     correct_row(S, i, acc + 3 * q, jerk + 3 * q, t_new, tick, eta, lmin, lmax, st);
@@ -413,26 +482,45 @@ cudaError_t iota_launch(int32_t *a, int64_t n, cudaStream_t s, int64_t *launches
     return cudaGetLastError();
 }
 
+cudaError_t mass_jstream_launch(const State &S, const JStream &J, cudaStream_t s, int64_t *launches)
+{
+    mass_jstream_kernel<<<blocks_for(S.n, kThreads, 152 * 8), kThreads, 0, s>>>(S, J);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t aos_from_soa_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches)
+{
+    aos_from_soa_kernel<<<blocks_for(n, kThreads, 152 * 8), kThreads, 0, s>>>(J, n);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
                            cudaStream_t s, int64_t *launches, const long long *t_dev)
 {
     // FP64 per particle: small n spread over more SMs (GB300's FP64 rate per SM is low)
     const int tpb = S.n >= 152 * 128 ? kThreads : 32;
-    predict_kernel<<<blocks_for(S.n, tpb, 152 * 64 * (kThreads / tpb)), tpb, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax),
-                                                                                   lo_parts, t_dev);
+    const unsigned grid = static_cast<unsigned>(blocks_for(S.n, tpb, 152 * 64 * (kThreads / tpb)));
+    if (S.n >= 152 * 128)
+        predict_kernel<true><<<grid, tpb, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax), lo_parts, t_dev);
+    else
+        predict_kernel<false><<<grid, tpb, 0, s>>>(S, J, t_new, ldexp(1.0, -lmax), lo_parts, t_dev);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act, const double *acc,
                            const double *jerk, int64_t t_new, double eta, int lmin, int lmax, DevStatus *st,
-                           cudaStream_t s, int64_t *launches, const SchedOut *sched_dev)
+                           cudaStream_t s, int64_t *launches, const SchedOut *sched_dev, const float *part,
+                           int split, bool two_word)
 {
     if (n_act <= 0) return cudaSuccess;
     // FP64-heavy rows: small blocks spread over more SMs (GB300's FP64 rate per SM is low)
     const int tpb = n_act >= 152 * 128 ? 128 : 32;
     correct_kernel<<<blocks_for(n_act, tpb), tpb, 0, s>>>(S, active, n_act, acc, jerk, t_new, ldexp(1.0, -lmax),
-                                                          eta, lmin, lmax, st, sched_dev);
+                                                          eta, lmin, lmax, st, sched_dev, part, split,
+                                                          two_word ? 1 : 0);
     ++*launches;
     return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ enum : unsigned {
     kFlagDtMin = 2u,
     kFlagTimeout = 4u,
     kFlagBadIndex = 8u,
+    kFlagDebugBounds = 16u,  // -DNB_DEBUG builds: an internal index check failed (the access was skipped)
 };
 
 struct DevStatus {
@@ -45,7 +46,25 @@ struct DevStatus {
     int bad_index;
     unsigned long long below_min;
     unsigned long long nonfinite;
+    int debug_site;  // -DNB_DEBUG builds: which check failed (sites listed at NB_CHECK's uses)
 };
+
+// Device-side index checks of the debug build (-DNB_DEBUG): a failed check
+// records kFlagDebugBounds and its site in the status word and skips the
+// access; it never traps.  In other builds NB_CHECK is true and costs nothing.
+#ifdef NB_DEBUG
+__device__ __forceinline__ bool nb_debug_check(const bool ok, DevStatus *st, const int site)
+{
+    if (!ok) {
+        atomicOr(&st->flags, static_cast<unsigned>(kFlagDebugBounds));
+        st->debug_site = site;
+    }
+    return ok;
+}
+#define NB_CHECK(cond, st, site) nb_debug_check((cond), (st), (site))
+#else
+#define NB_CHECK(cond, st, site) true
+#endif
 
 // FP64 master state, structure of arrays: component c of particle i is x[c][i].
 struct State {
@@ -71,6 +90,7 @@ struct JStream {
     // force kernel copies its tiles straight from here; NULL (no-alloc callers) means AoS only.
     float *soa;
     int64_t n_pad;
+    bool aos;  // the predictor also writes posm, vel, poslo (vello): a kernel of the context reads them
 };
 constexpr int kSoaArrays = 10;
 
@@ -80,15 +100,22 @@ struct ForceConfig {
     int split;            // j-ranges (gridDim.y)
     int tiles_per_split;  // tiles of kJTile j per range
     int n_iblk;           // i-blocks (gridDim.x)
+    int jsub = 1;         // threads per row, each taking 1/jsub of every tile (1 or 4)
 };
+// The j-subgroup shape: 256 threads, 64 rows of 4 subgroups (packed plain and compensated modes).
+constexpr int kJSubThreads = 256;
+constexpr int kJSub = 4;
+constexpr int kJSubMinRows = 512;   // automatic shape: j-subgroups from this many rows on,
+constexpr int kJSubMinTiles = 64;   // for streams of at least this many tiles (n >= 16384)
 
 // ---- force.cu ----
 extern int g_skip_first_copy;  // test hook: force kernels leave out their first tile copy
 
 // Picks the launch shape for n_act active particles against n_pad j.
 // req_* > 0 override the automatic choice.
+// req_jsub: 0 automatic, 1 one thread per row, 4 four (256 threads, one i each).
 int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_threads,
-                 int req_ipt, int req_split, ForceConfig *cfg);
+                 int req_ipt, int req_split, ForceConfig *cfg, int req_jsub = 0);
 // Whether this mode's force kernels honour ForceParams::n_act_dev (the packed kernels).
 bool force_reads_device_rows(int mode);
 // Scratch bytes needed for partial sums when cfg.split > 1 (0 otherwise).
@@ -97,10 +124,18 @@ size_t force_partial_bytes(int mode, const ForceConfig &cfg, int64_t n_act);
 // split > 1).  acc/jerk: n_act*3, pot: n_act, device doubles.  With n_act_dev
 // (packed plain/compensated kernels only) the launch is sized for n_act rows
 // and the kernels read the actual block size from *n_act_dev on the device.
+// With reduce = false and force_partials_fused(mode, cfg) the j-range partial
+// sums are left in `partials` for the corrector to add (correct_launch).
 cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *active,
                          int64_t n_act, double eps2, const ForceConfig &cfg, double *acc,
                          double *jerk, double *pot, void *partials, DevStatus *st,
-                         cudaStream_t s, int64_t *launches, const long long *n_act_dev = nullptr);
+                         cudaStream_t s, int64_t *launches, const long long *n_act_dev = nullptr,
+                         bool reduce = true);
+// Splits below this are added by the block-step corrector itself (in the order of
+// the one-thread-per-row reduction), which saves a dependent kernel per block.
+constexpr int kFusedSplitMax = 8;
+// Whether a block step of this mode and shape hands its partials to the corrector.
+bool force_partials_fused(int mode, const ForceConfig &cfg);
 
 // ---- force_ds.cu ----
 int force_occupancy_ds();
@@ -118,10 +153,14 @@ struct SchedOut;
 // t_dev / sched_dev (graph replays): the time and block size are read on the device.
 cudaError_t predict_launch(const State &S, const JStream &J, int64_t t_new, int lmax, int lo_parts,
                            cudaStream_t s, int64_t *launches, const long long *t_dev = nullptr);
+// With `part` (split > 1), row q's forces are the sum of its j-range partials
+// (part[split][7 or 14][n_act], two_word: hi and lo words), added in ascending
+// range order in FP64 as the one-thread-per-row reduction does; acc, jerk unused.
 cudaError_t correct_launch(const State &S, const int32_t *active, int64_t n_act,
                            const double *acc, const double *jerk, int64_t t_new, double eta,
                            int lmin, int lmax, DevStatus *st, cudaStream_t s, int64_t *launches,
-                           const SchedOut *sched_dev = nullptr);
+                           const SchedOut *sched_dev = nullptr, const float *part = nullptr, int split = 0,
+                           bool two_word = false);
 // a, k <- the full force at t = 0 (acc, jerk: n*3), t <- 0, level from Eq. (initTimestep).
 cudaError_t init_levels_launch(const State &S, const double *acc, const double *jerk,
                                double eta_init, int lmin, int lmax, DevStatus *st,
@@ -173,6 +212,13 @@ cudaError_t phi_ds_launch(const State &S, double eps2, double *phi, cudaStream_t
 // min and max of t over all particles (out: 2 unsigned long long).
 cudaError_t time_range_launch(const State &S, unsigned long long *out, cudaStream_t s,
                               int64_t *launches);
+
+// Writes the masses of the j-stream (SoA and float4 forms) once, at set-up.
+cudaError_t mass_jstream_launch(const State &S, const JStream &J, cudaStream_t s, int64_t *launches);
+// posm, vel, poslo from the SoA stream (for readers of the float4 form when J.aos is off).
+cudaError_t aos_from_soa_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches);
+// Whether this mode's kernels read the float4 j-stream (the predictor must write it).
+bool force_needs_aos(int mode);
 
 // Fills j-stream entries n .. n_pad-1 with massless particles at kPadPosition.
 cudaError_t pad_jstream_launch(const JStream &J, int64_t n, cudaStream_t s, int64_t *launches);

@@ -140,7 +140,7 @@ extern "C" int nbody_force_noalloc(const float *posm, const float *vel, const fl
     const int64_t n_pad = (n + kJTile - 1) / kJTile * kJTile;
     const int64_t nc = mode == NBODY_MODE_COMP ? 14 : 7;
     ForceConfig cfg{};
-    if (force_choose(mode, n_act, n_pad, sm_count, 0, 0, 0, &cfg) != NBODY_OK)
+    if (force_choose(mode, n_act, n_pad, sm_count, 0, 0, 0, &cfg, 1) != NBODY_OK)  // the caller's stream is float4 only
         return fail(NBODY_EINVAL, "nbody_force_noalloc: no launch shape");
     // Always at least two j-ranges (the scratch is used), at most what fits.
     const int64_t fit = static_cast<int64_t>(kNoAllocPartialFloats) / (nc * n_act);

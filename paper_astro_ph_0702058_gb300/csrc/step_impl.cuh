@@ -8,15 +8,54 @@
 
 namespace nb {
 
+// Step factors of the predictor: dt/2 (exact) and dt/3.
+struct PredDt {
+    double dt, half, third;
+};
+__device__ __forceinline__ PredDt pred_dt(const double dt) { return {dt, 0.5 * dt, __dmul_rn(dt, 1.0 / 3.0)}; }
+
 // Predictor of Sect. 2 for one component, in Horner form with explicit
 // roundings so that the predictor and the corrector kernels give the same
-// bits:  x_p = x + dt (v + dt (a/2 + dt k/6)),  v_p = v + dt (a + dt k/2).
-__device__ __forceinline__ void predict_dim(double x, double v, double a, double k, double dt,
+// bits:  x_p = x + dt (v + dt/2 (a + dt/3 k)),  v_p = v + dt (a + dt/2 k),
+// i.e. x + v dt + a dt^2/2 + k dt^3/6 and v + a dt + k dt^2/2 in five fused
+// multiply-adds (GB300's FP64 pipe is ~1/75 of its FP32 pipe).
+__device__ __forceinline__ void predict_dim(double x, double v, double a, double k, const PredDt &d,
                                             double &xp, double &vp)
 {
-    const double k6 = __dmul_rn(k, 1.0 / 6.0);
-    xp = __fma_rn(dt, __fma_rn(dt, __fma_rn(dt, k6, 0.5 * a), v), x);
-    vp = __fma_rn(dt, __fma_rn(dt, 0.5 * k, a), v);
+    xp = __fma_rn(d.dt, __fma_rn(d.half, __fma_rn(d.third, k, a), v), x);
+    vp = __fma_rn(d.dt, __fma_rn(d.half, k, a), v);
+}
+
+// Round-to-nearest-even double -> float, and exact float -> double, on the
+// integer pipe: GB300 converts at the FP64 rate (~1.8 per clock per SM, the
+// predictor's bound).  IEEE 754 binary64 -> binary32: the 52-bit fraction keeps
+// its top 23 bits, rounded by the 29 dropped ones (ties to even); a carry out
+// of the fraction moves into the exponent, which the addition below does.
+// Results outside the normal float range (zero, subnormal, overflow, Inf, NaN)
+// take the hardware conversion; every value the predictor writes is normal or
+// zero.
+__device__ __forceinline__ float d2f_rn(const double d)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const int ef = static_cast<int>((b >> 52) & 0x7ffull) - 1023 + 127;
+    if (ef < 1 || ef > 254) return __double2float_rn(d);
+    const unsigned long long frac = b & ((1ull << 52) - 1);
+    unsigned int keep = static_cast<unsigned int>(frac >> 29);
+    const unsigned int rest = static_cast<unsigned int>(frac & ((1u << 29) - 1));
+    keep += (rest > (1u << 28)) | ((rest == (1u << 28)) & (keep & 1u));
+    const unsigned int bits = (static_cast<unsigned int>(b >> 63) << 31) + ((static_cast<unsigned int>(ef) << 23) + keep);
+    return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double f2d(const float f)
+{
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int ef = (b >> 23) & 0xffu;
+    if (ef == 0u || ef == 255u) return static_cast<double>(f);
+    const unsigned long long bits = (static_cast<unsigned long long>(b >> 31) << 63) |
+                                    (static_cast<unsigned long long>(ef - 127 + 1023) << 52) |
+                                    (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+    return __longlong_as_double(static_cast<long long>(bits));
 }
 
 __device__ __forceinline__ double norm3(const double *u)
@@ -66,12 +105,13 @@ __device__ __forceinline__ void correct_row(const State &S, const int64_t i, con
     const double dt4 = dt3 * dt;
     double ap[3], kp[3], a2e[3], a3[3];
     bool finite = true;
+    const PredDt pd = pred_dt(dt);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double a = S.a[c][i];
         const double k = S.k[c][i];
         double xp, vp;
-        predict_dim(S.x[c][i], S.v[c][i], a, k, dt, xp, vp);
+        predict_dim(S.x[c][i], S.v[c][i], a, k, pd, xp, vp);
         ap[c] = ap_in[c];
         kp[c] = kp_in[c];
         const double da = a - ap[c];  // Delta a = a - a_p
