@@ -447,19 +447,27 @@ def bench_reference(args):
 
 
 def force_only(args):
-    """One nbody_force on all N particles per mode, untimed: the launch that profilers capture."""
+    """One nbody_force per mode, untimed: the launch that profilers capture.  A Plummer sphere of
+    --n particles (seed --seed, softening --eps2; default the benchmark's), after nbody_init's full
+    force; the call covers all particles, or --rows of them (a seeded sorted uniform sample)."""
     import torch
 
     from paper_astro_ph_0702058_gb300 import Simulation
-    from synthetic import plummer_sphere
-    m, x, v = plummer_sphere(args.n, SEED)
-    act = torch.arange(args.n, dtype=torch.int32, device="cuda")
+    from synthetic import active_subset, plummer_sphere
+    seed = SEED if args.seed is None else args.seed
+    eps2 = EPS2 if args.eps2 is None else args.eps2
+    m, x, v = plummer_sphere(args.n, seed)
+    rows = args.n if args.rows is None else args.rows
+    if rows == args.n:
+        act = torch.arange(args.n, dtype=torch.int32, device="cuda")
+    else:
+        act = torch.from_numpy(active_subset(args.n, rows, 2)).to("cuda")
     for mode in args.modes.split(","):
-        with Simulation(m, x, v, EPS2, mode=mode) as sim:
+        with Simulation(m, x, v, eps2, mode=mode) as sim:
             sim.predict(0.0)
-            sim.force(act, args.n)
+            sim.force(act, rows)
             sim.sync()
-    print(json.dumps({"force_only": args.n, "modes": args.modes}))
+    print(json.dumps({"force_only": args.n, "rows": rows, "seed": seed, "eps2": eps2, "modes": args.modes}))
 
 
 def c2_sweep(args):
@@ -527,8 +535,11 @@ def c1_run(args):
     n, eps2, t_end = 1024, (1.0 / 256) ** 2, 0.125
     m, x, v = plummer_sphere(n, 1)
     torch.cuda.set_device(0)
+    from paper_astro_ph_0702058_gb300 import nbody_debug_step_graphs
+    t_end = args.t_end if args.t_end is not None else t_end
+    nbody_debug_step_graphs(args.step_graphs)
     rows = []
-    for mode in ("plain", "comp", "sorted", "ds"):
+    for mode in args.c1_modes.split(","):
         with Simulation(m, x, v, eps2, eta=0.01, lmin=6, lmax=26, mode=mode) as sim:
             e0 = sum(sim.energy())
             sim.sync()
@@ -542,6 +553,11 @@ def c1_run(args):
         # device-side loop ran without a host round trip
         rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "energy_error": abs((e1 - e0) / e0),
                      "graph_blocks": int(st["graph_blocks"]), "loop_blocks": int(st["loop_blocks"])})
+    nbody_debug_step_graphs(2)
+    if args.no_cpu_baseline:
+        print(json.dumps({"workload": "c1", "n": n, "eps2": eps2, "eta": 0.01, "t_end": t_end, "rows": rows}),
+              flush=True)
+        return
     # cpu_baseline leg: the FP64 oracle's own run of C1 on the host cores
     oracle.set_threads(len(os.sched_getaffinity(0)))
     st = oracle.State(m, x, v, eps2, 0.01, lmin=6, lmax=26).init()
@@ -730,6 +746,13 @@ def main(argv=None):
     ap.add_argument("--ens-sample", type=int, default=32,
                     help="clusters run one context each, for comparison (0: skip the comparison)")
     ap.add_argument("--ens-mode", default="comp")
+    ap.add_argument("--rows", type=int, default=None, help="--force-only: rows of the call (default: all)")
+    ap.add_argument("--seed", type=int, default=None, help="--force-only: seed of the sphere (default 3)")
+    ap.add_argument("--eps2", type=float, default=None, help="--force-only: softening squared (default 1e-6)")
+    ap.add_argument("--c1-modes", default="plain,comp,sorted,ds", help="c1: the force modes to run")
+    ap.add_argument("--step-graphs", type=int, default=2,
+                    help="c1: 0 separate launches per block, 1 one graph replay per block, 2 the device-side loop")
+    ap.add_argument("--t-end", type=float, default=None, help="c1: end time (a multiple of 1/64; default 1/8)")
     args = ap.parse_args(argv)
     if args.force_only:
         force_only(args)

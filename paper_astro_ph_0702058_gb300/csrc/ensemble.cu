@@ -187,20 +187,21 @@ __global__ void ens_predict_kernel(const EnsDev E, double tick, int comp)
         if (E.n_act[c] == 0) continue;
         const double dt = static_cast<double>(E.t_blk[c] - E.S.t[i]) * tick;
         double xp[3], vp[3];
-#pragma unroll
         const PredDt pd = pred_dt(dt);
+#pragma unroll
         for (int q = 0; q < 3; ++q) predict_dim(E.S.x[q][i], E.S.v[q][i], E.S.a[q][i], E.S.k[q][i], pd, xp[q], vp[q]);
         const int64_t j = E.joff[c] + (i - E.off[c]);
-        const float hx = __double2float_rn(xp[0]), hy = __double2float_rn(xp[1]), hz = __double2float_rn(xp[2]);
-        const float hm = __double2float_rn(E.S.m[i]);
-        const float hvx = __double2float_rn(vp[0]), hvy = __double2float_rn(vp[1]), hvz = __double2float_rn(vp[2]);
+        // the roundings on the integer pipe (d2f_rn: the same bits as the hardware conversion)
+        const float hx = d2f_rn(xp[0]), hy = d2f_rn(xp[1]), hz = d2f_rn(xp[2]);
+        const float hm = d2f_rn(E.S.m[i]);
+        const float hvx = d2f_rn(vp[0]), hvy = d2f_rn(vp[1]), hvz = d2f_rn(vp[2]);
         E.J.posm[j] = make_float4(hx, hy, hz, hm);
         E.J.vel[j] = make_float4(hvx, hvy, hvz, 0.f);
         float lx = 0.f, ly = 0.f, lz = 0.f;
         if (comp) {
-            lx = __double2float_rn(xp[0] - static_cast<double>(hx));
-            ly = __double2float_rn(xp[1] - static_cast<double>(hy));
-            lz = __double2float_rn(xp[2] - static_cast<double>(hz));
+            lx = d2f_rn(xp[0] - f2d(hx));
+            ly = d2f_rn(xp[1] - f2d(hy));
+            lz = d2f_rn(xp[2] - f2d(hz));
             E.J.poslo[j] = make_float4(lx, ly, lz, 0.f);
         }
         float *a = E.J.soa + j;

@@ -32,11 +32,16 @@ def _intact(torch, buf, rows):
 @pytest.mark.parametrize("mode", ["plain", "comp", "ds"])
 @pytest.mark.parametrize("n,n_act,shape", [(1, 1, (0, 0, 0)), (17, 5, (0, 0, 0)), (257, 257, (64, 1, 2)),
                                            (3000, 1111, (128, 2, 3)), (3000, 99, (256, 4, 0)),
-                                           (12000, 8192, (0, 0, 0))])
+                                           (12000, 8192, (0, 0, 0)), (3000, 1000, (0, -4, 0)),
+                                           (20000, 1003, (0, 0, 0))])
 def test_force_writes_exactly_its_rows(torch, mode, n, n_act, shape):
+    """(i_block -4 stands for the j-subgroup shape, j_sub = 4.)"""
     from paper_astro_ph_0702058_gb300 import Simulation
     m, x, v = plummer_sphere(n, 90 + n % 7)
-    kw = {} if mode == "ds" else dict(j_tile=shape[0], i_block=shape[1], j_split=shape[2])
+    if shape[1] < 0:
+        kw = {} if mode == "ds" else dict(j_sub=-shape[1], j_split=shape[2])
+    else:
+        kw = {} if mode == "ds" else dict(j_tile=shape[0], i_block=shape[1], j_split=shape[2])
     act = torch.from_numpy(active_subset(n, n_act, 4)).cuda()
     acc, jerk, pot = _canary(torch, n_act, 3), _canary(torch, n_act, 3), _canary(torch, n_act, 1)
     with Simulation(m, x, v, EPS2, mode=mode, **kw) as sim:

@@ -115,6 +115,14 @@ def test_force_every_launch_shape(torch, mode):
                 st = sim.stats()
             assert (st["last_threads"], st["last_i_per_thread"], st["last_j_split"]) == (threads, ipt, split)
             check_force(mode, m, x, v, EPS2, act, got, ref, f"shape {threads}x{ipt} split {split}")
+    # the j-subgroup shape (256 threads: 64 rows x 4 tile quarters), with its own split rule and fixed splits
+    for split in (0, 1, 3, 12):
+        with _sim(m, x, v, EPS2, mode, j_sub=4, j_split=split) as sim:
+            sim.predict(0.0)
+            got = gpu_force(sim, act)
+            st = sim.stats()
+        assert (st["last_threads"], st["last_j_sub"]) == (256, 4) and (split == 0 or st["last_j_split"] == split)
+        check_force(mode, m, x, v, EPS2, act, got, ref, f"j-subgroups split {split}")
 
 
 @pytest.mark.parametrize("mode", ["plain", "comp"])
