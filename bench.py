@@ -549,11 +549,13 @@ def c1_run(args):
             wall = time.perf_counter() - t0
             e1 = sum(sim.energy())
             st = sim.stats()
-        # graph_blocks: blocks run inside step-graph replays; loop_blocks: of those, the ones the
-        # device-side loop ran without a host round trip
-        rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "energy_error": abs((e1 - e0) / e0),
+        # cluster_blocks: blocks run by the one-cluster kernel; graph_blocks: blocks run inside
+        # step-graph replays; loop_blocks: of those, the ones the device-side loop ran without a host
+        # round trip
+        rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "us_per_block": wall / max(blocks, 1) * 1e6,
+                     "energy_error": abs((e1 - e0) / e0), "cluster_blocks": int(st["cluster_blocks"]),
                      "graph_blocks": int(st["graph_blocks"]), "loop_blocks": int(st["loop_blocks"])})
-    nbody_debug_step_graphs(2)
+    nbody_debug_step_graphs(3)
     if args.no_cpu_baseline:
         print(json.dumps({"workload": "c1", "n": n, "eps2": eps2, "eta": 0.01, "t_end": t_end, "rows": rows}),
               flush=True)
@@ -750,8 +752,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=None, help="--force-only: seed of the sphere (default 3)")
     ap.add_argument("--eps2", type=float, default=None, help="--force-only: softening squared (default 1e-6)")
     ap.add_argument("--c1-modes", default="plain,comp,sorted,ds", help="c1: the force modes to run")
-    ap.add_argument("--step-graphs", type=int, default=2,
-                    help="c1: 0 separate launches per block, 1 one graph replay per block, 2 the device-side loop")
+    ap.add_argument("--step-graphs", type=int, default=3,
+                    help="c1: 0 separate launches per block, 1 one graph replay per block, 2 the device-side loop, "
+                         "3 the one-cluster block-step kernel")
     ap.add_argument("--t-end", type=float, default=None, help="c1: end time (a multiple of 1/64; default 1/8)")
     args = ap.parse_args(argv)
     if args.force_only:

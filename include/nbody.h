@@ -236,6 +236,7 @@ typedef struct {
     int64_t graph_blocks;  /* block steps nbody_step ran inside a replayed CUDA graph */
     int64_t loop_blocks;   /* of those, the ones the device-side loop added (no host round trip) */
     int last_j_sub;        /* threads per row of the last force kernel (1 or 4)    */
+    int64_t cluster_blocks; /* block steps nbody_step ran in the one-cluster kernel */
 } nbody_stats;
 
 int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);
@@ -272,12 +273,20 @@ void nbody_debug_skip_tile_copy(int on);
  *      fewer than 1024 blocks to the replay's first; the host then reads back
  *      the next block.  Without while-nodes
  *      it acts as 1.
+ *   3  (default) as 2, except that in the plain and compensated modes, with
+ *      automatic force shapes (j_tile, i_block, j_split, j_sub all 0) and
+ *      n_pad <= 4096, every block runs in one launch of a kernel of one
+ *      thread-block cluster (16 or 8 CTAs) that repeats schedule, predictor,
+ *      force and corrector on the device while the next block is due by
+ *      t_end, no error flag is raised and max_steps allows (at most 4096
+ *      blocks per launch).  Its forces are the same pair terms summed in
+ *      another order, so its results differ from levels 0-2 in the last bits.
  * A context captures its graph in the form of the level in force when it
  * builds it (once, and again only if its scratch buffer moves); a loop graph
  * run at level 1 stops after each block.
  * The graph is used only when its launch shape is the one the separate
- * launches would take, so all three give the same results bit for bit.
- * Values outside 0..2 are clamped. */
+ * launches would take, so levels 0-2 give the same results bit for bit.
+ * Values outside 0..3 are clamped. */
 void nbody_debug_step_graphs(int level);
 
 /* ------------------------------------------------------------ differentiation

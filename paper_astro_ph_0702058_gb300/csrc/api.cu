@@ -22,8 +22,9 @@ thread_local char g_err[512] = "";
 int g_fail_alloc = 0;    // allocation-failure injection countdown (test hook)
 // nbody_step's small blocks (test switch): 0 separate launches, 1 one graph
 // replay per block, 2 a device-side loop of blocks in each replay
-int g_step_graphs = 2;
+int g_step_graphs = 3;
 constexpr int64_t kLoopCap = 1024;  // blocks one replay of the loop may run
+constexpr int64_t kClusterCap = 4096;  // blocks one launch of the cluster kernel may run
 
 int fail(int code, const char *fmt, ...)
 {
@@ -769,6 +770,16 @@ unsigned loop_stop_flags(const nbody_ctx *c)
     return kFlagTimeout | kFlagBadIndex | kFlagNonfinite | kFlagDebugBounds | (c->p.strict ? kFlagDtMin : 0u);
 }
 
+// Blocks of this context may run in the one-cluster kernel (level 3).
+bool cluster_steps(const nbody_ctx *c)
+{
+    if (g_step_graphs < 3 || (c->p.mode != NBODY_MODE_PLAIN && c->p.mode != NBODY_MODE_COMP)) return false;
+    if (c->p.j_tile != 0 || c->p.i_block != 0 || c->p.j_split != 0 || c->p.j_sub != 0) return false;
+    if (!c->J.soa || c->n_pad > kClMaxPad) return false;
+    const int C = cluster_step_size(c->p.mode);
+    return C > 0 && c->n_pad / C <= kClMaxChunk;
+}
+
 // Builds the replayed graph: the block step as the body of a while-node, whose
 // last kernel decides whether the next block runs in the same replay, then the
 // read-back of the next block, the status and the loop control.  Without
@@ -907,7 +918,43 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     }
     int64_t tb = 0, na = 0;
     r = schedule_internal(c, &tb, &na);
+    const bool cluster = cluster_steps(c);
+    bool cluster_declined = false;  // the cluster kernel ran none of the blocks it was offered
     while (r == NBODY_OK && tb <= tend && !(max_steps > 0 && done >= max_steps)) {
+        if (cluster && !cluster_declined) {
+            StepLoop *L = c->loop_host;
+            const int64_t left = max_steps > 0 ? max_steps - done : kClusterCap;
+            NB_CUDA(cluster_step_launch(c->p.mode, c->S, c->J, c->eps2, c->p.eta, c->p.lmin, c->p.lmax, tend,
+                                        std::min(left, kClusterCap), c->n, c->t_pred, loop_stop_flags(c), c->st,
+                                        c->sched_out, c->loop_dev, c->act_sched, c->act_corr, c->s,
+                                        &c->stats.kernel_launches),
+                    "cluster block-step launch");
+            NB_CUDA(cudaMemcpyAsync(L, c->loop_dev, sizeof(StepLoop), cudaMemcpyDeviceToHost, c->s), "loop read-back");
+            NB_CUDA(cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, c->s),
+                    "schedule read-back");
+            NB_CUDA(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->s),
+                    "status read-back");
+            NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+            const int64_t blocks = L->blocks;
+            c->stats.force_calls += blocks;
+            c->stats.pairs += L->rows * (c->n - 1);
+            c->stats.blocks += blocks;
+            c->stats.cluster_blocks += blocks;
+            if (blocks > 0) {
+                c->t_max = std::max(c->t_max, static_cast<int64_t>(L->last_t));
+                c->t_pred = L->last_t;
+                c->pred_valid = false;
+                c->force_n_act = -1;
+            }
+            done += blocks;
+            r = absorb_status(c);
+            if (r != NBODY_OK) break;
+            tb = c->sched_host->t_blk;
+            na = c->sched_host->n_act;
+            cluster_declined = blocks == 0;  // that block takes the path below once
+            continue;
+        }
+        cluster_declined = false;
         ForceConfig cfg{};
         bool use_graph = g_step_graphs > 0 && packed && c->graph_rows > 0 && na <= c->graph_rows &&
                          force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block,
@@ -1121,6 +1168,6 @@ void nbody_debug_fail_alloc(int k) { g_fail_alloc = k > 0 ? k : 0; }
 
 void nbody_debug_skip_tile_copy(int on) { nb::g_skip_first_copy = on ? 1 : 0; }
 
-void nbody_debug_step_graphs(int level) { g_step_graphs = level < 0 ? 0 : (level > 2 ? 2 : level); }
+void nbody_debug_step_graphs(int level) { g_step_graphs = level < 0 ? 0 : (level > 3 ? 3 : level); }
 
 }  // extern "C"

@@ -1,0 +1,500 @@
+// Block steps of a small system inside one thread-block cluster: the block
+// time-step scheme of Sect. 2 (the next block time and its active particles,
+// the predictor, the force of Eq. (Force) on the active particles, the
+// corrector and Eq. (timestep)) repeated by one launch, the CTAs of the
+// cluster meeting at two hardware cluster barriers per block.
+//
+// At small n a block is latency: separate kernels for the schedule, the
+// predictor, the force and the corrector cost a few microseconds each even when
+// they have almost nothing to do.  Here CTA r of C owns the particles
+// [r chunk, (r+1) chunk), chunk = n_pad / C.  Per block:
+//   1. each CTA takes the earliest due tick t_i + dt_i over its particles that
+//      were not in the last block and the rows it corrected in the last block,
+//      and stores it into every CTA's shared memory; barrier A; every CTA takes
+//      the minimum, the block time (each CTA keeps the due ticks of its own
+//      particles in shared memory; a corrector stores a row's new one into its
+//      owner's);
+//   2. each CTA lists its active particles (ascending) in global memory,
+//      predicts all of its particles into the structure-of-arrays j-stream and
+//      stores its count into every CTA's shared memory; barrier C;
+//   3. the block's rows, in list order, are cut into C equal contiguous shares;
+//      each CTA copies the whole predicted j-stream into shared memory, computes
+//      the force on its share over all n j (T threads per row, T a power of
+//      two, taking groups of 4 j in turn; the T sums added in a fixed tree), and
+//      corrects its share: up to 8 rows in one warp, 4 lanes per row, else one
+//      row per lane of as few warps as possible.
+// GB300's FP64 unit is one per SM and takes ~19 cycles per warp instruction
+// whatever the number of active lanes (64-cycle latency, ~650-700 for a
+// division or square root), so the FP64 corrector runs with 32 rows per warp
+// and the rows are spread evenly over the cluster's SMs; the predictor rounds
+// to float on the integer pipe (d2f_rn, f2d: the same bits).  State written by
+// one CTA and read by another in a later block is read through L2 only.
+//
+// Every decision to go on or stop (block time past t_end, budget spent, a stop
+// flag, an empty block or one larger than rows_max) is taken from values every
+// CTA holds alike after a barrier, so all CTAs leave the loop together; the
+// status flags are read by CTA 0 between barriers A and C, when no corrector
+// runs, and passed on with its count.  No wait spins: the barriers are the
+// hardware's, and the loop runs at most `budget` blocks.
+//
+// The pair term and its 128-term folds are those of the packed force kernel
+// (force_x2.cuh); the per-thread sums of a row are added in double-single
+// (compensated) or FP32 (plain) arithmetic in a fixed order.  The predictor and
+// the corrector are those of step_impl.cuh, so the state a block leaves differs
+// from the separate kernels' only by the summation order of its forces.
+#include <cooperative_groups.h>
+
+#include "force_x2.cuh"
+#include "step_impl.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace nb {
+
+namespace {
+
+constexpr int kClThreads = 512;
+constexpr int kClWarps = kClThreads / 32;
+constexpr int kClMaxC = 16;
+static_assert(kClMaxChunk <= kClThreads, "one own particle per thread");
+
+struct ClArgs {
+    State S;
+    float *soa;  // the predicted j-stream (kSoaArrays x n_pad); padding entries stay as set up
+    int64_t n_pad;
+    float eps2;
+    double tick, eta;
+    int lmin, lmax;
+    long long t_end, budget, rows_max, last_t;
+    unsigned stop_flags;
+    DevStatus *st;
+    SchedOut *sched_out;
+    StepLoop *L;
+    int32_t *act_out;  // the block's list (n), for the host
+    int32_t *lists;    // scratch (n): CTA r's active particles at r chunk ..
+};
+
+// Symmetric merge of two double-single sums (hi, lo) + (h2, l2): Knuth's
+// TwoSum of the high words, the low words and its error added after.
+__device__ __forceinline__ void ds_merge(float &hi, float &lo, const float h2, const float l2)
+{
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArgs A)
+{
+    constexpr int NA = SoaTile<MODE>::NA;
+    constexpr bool DSW = MODE == kModeComp;  // two-word sums
+    extern __shared__ __align__(16) float jsm[];  // NA x n_pad: the predicted j-stream
+    __shared__ unsigned long long x_min[kClMaxC];  // earliest due tick of each CTA (stored by that CTA)
+    __shared__ int x_cnt[kClMaxC];                 // active count of each CTA (stored by that CTA)
+    __shared__ unsigned x_flags;                   // status flags of this block (stored by CTA 0)
+    __shared__ int row_idx[kClMaxChunk];           // this CTA's share of the block's rows
+    __shared__ float f_hi[kClMaxChunk][6], f_lo[kClMaxChunk][6];  // their acc and jerk sums
+    __shared__ int warp_tot[kClWarps];
+    __shared__ float wred[kClWarps][6][2];
+    __shared__ unsigned long long red_u64[32];
+    __shared__ int b_pre[kClMaxC + 1];
+    __shared__ unsigned long long due_c[kClMaxChunk];  // due ticks of this CTA's particles
+    __shared__ unsigned long long due_r[kClMaxChunk];  // new due ticks of the rows it corrected last
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = static_cast<int>(cl.num_blocks());
+    const int rank = static_cast<int>(cl.block_rank());
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const State &S = A.S;
+    const int64_t n = S.n;
+    const int np = static_cast<int>(A.n_pad);
+    const int chunk = np / C;
+    const int lo_i = rank * chunk;
+    const int hi_i = static_cast<int>(min(static_cast<int64_t>(lo_i + chunk), n));
+    const f2_t E2 = f2_pack(A.eps2, A.eps2);
+    const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
+
+    const int i = lo_i + tid;  // this thread's own particle
+    const bool mine = tid < chunk && i < hi_i;
+    if (mine)
+        due_c[tid] = static_cast<unsigned long long>(ld_state<true>(S.t + i) +
+                                                     (int64_t(1) << (A.lmax - ld_state<true>(S.level + i))));
+    cl.sync();  // every CTA of the cluster runs before any stores into another's shared memory
+    long long done = 0, rows = 0, last_t = A.last_t;
+    unsigned long long tb = 0;
+    int na = 0, cnt_last = 0;
+    bool hit = false;  // this thread's particle was in the last block
+    for (;;) {
+        // 1. the earliest due tick over this CTA's particles that were not in the last
+        //    block (unchanged) and the rows it corrected (their new ones), stored into every CTA
+        unsigned long long m = (mine && !hit) ? due_c[tid] : ~0ull;
+        if (tid < cnt_last) m = due_r[tid] < m ? due_r[tid] : m;
+        m = block_reduce(m, MinOp(), red_u64, ~0ull);
+        if (warp == 0 && lane < C) *cl.map_shared_rank(&x_min[rank], lane) = m;
+        cl.sync();  // barrier A: every corrector of the last block has finished
+        if (rank == 0 && tid == 0) x_flags = __ldcg(&A.st->flags);  // stored into the others below
+        tb = ~0ull;
+        for (int r = 0; r < C; ++r) tb = x_min[r] < tb ? x_min[r] : tb;
+
+        // 2. this CTA's active particles (ascending) and its particles predicted to tb
+        {
+            hit = mine && due_c[tid] == tb;
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) warp_tot[warp] = __popc(mask);
+            if (mine) {  // the state through L2: another CTA may have corrected it
+                const PredDt pd = pred_dt(static_cast<double>(static_cast<int64_t>(tb) - ld_state<true>(S.t + i)) * A.tick);
+                float *a = A.soa + i;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double xp, vp;
+                    predict_dim(ld_state<true>(S.x[c] + i), ld_state<true>(S.v[c] + i), ld_state<true>(S.a[c] + i),
+                                ld_state<true>(S.k[c] + i), pd, xp, vp);
+                    const float h = d2f_rn(xp);
+                    a[c * np] = h;
+                    a[(4 + c) * np] = d2f_rn(vp);
+                    if (DSW) a[(7 + c) * np] = d2f_rn(xp - f2d(h));  // the difference is exact
+                }
+            }
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int k = 0; k < kClWarps; ++k) {
+                before += k < warp ? warp_tot[k] : 0;
+                total += warp_tot[k];
+            }
+            if (hit) A.lists[lo_i + before + __popc(mask & ((1u << lane) - 1u))] = i;
+            if (warp == 0 && lane < C) {
+                *cl.map_shared_rank(&x_cnt[rank], lane) = total;
+                if (rank == 0) *cl.map_shared_rank(&x_flags, lane) = x_flags;
+            }
+        }
+        cl.sync();  // barrier C: the lists and the j-stream are complete, the counts and flags stored
+        int pre = 0;
+        for (int r = 0; r < C; ++r) pre += x_cnt[r];
+        na = pre;
+        const bool go = done < A.budget && (x_flags & A.stop_flags) == 0u && static_cast<long long>(tb) <= A.t_end &&
+                        na > 0 && na <= A.rows_max;
+        // this CTA's share of the rows in list order, and the list for the host
+        const int p0 = static_cast<int>(static_cast<long long>(rank) * na / C);
+        const int p1 = static_cast<int>(static_cast<long long>(rank + 1) * na / C);
+        const int cnt = p1 - p0;
+        if (tid == 0) {
+            int acc = 0;
+            for (int r = 0; r < C; ++r) {
+                b_pre[r] = acc;
+                acc += x_cnt[r];
+            }
+            b_pre[C] = acc;
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            const int p = p0 + tid;
+            int o = 0;
+            while (o + 1 < C && b_pre[o + 1] <= p) ++o;
+            const int r = __ldcg(A.lists + o * chunk + (p - b_pre[o]));
+            row_idx[tid] = r;
+            A.act_out[p] = r;
+        }
+        if (!go) break;
+
+        // 3. the j-stream into shared memory (L2 reads: other CTAs wrote it)
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(A.soa);
+            float4 *dst = reinterpret_cast<float4 *>(jsm);
+            const int nv = NA * np / 4;
+            for (int k = tid; k < nv; k += kClThreads) dst[k] = __ldcg(src + k);
+        }
+        __syncthreads();
+        if (cnt > 0) {
+            // T threads per row: the largest power of two with T cnt <= threads whose
+            // j-share n_pad / T is a multiple of 8
+            int T = kClThreads;
+            while (T > 1 && (T * cnt > kClThreads || (np / 8) % T != 0)) T >>= 1;
+            const int rpp = kClThreads / T;
+            const int L = np / T;
+            const int TW = T < 32 ? T : 32;
+            for (int q0 = 0; q0 < cnt; q0 += rpp) {
+                const int rr = q0 + tid / T;
+                const int sub = tid % T;
+                const bool live = rr < cnt;
+                const int gi = live ? row_idx[rr] : -1;
+                const int li = live ? gi : 0;
+                I2 I;
+                I.x = f2_pack(jsm[li], jsm[li]);
+                I.y = f2_pack(jsm[np + li], jsm[np + li]);
+                I.z = f2_pack(jsm[2 * np + li], jsm[2 * np + li]);
+                I.vx = f2_pack(jsm[4 * np + li], jsm[4 * np + li]);
+                I.vy = f2_pack(jsm[5 * np + li], jsm[5 * np + li]);
+                I.vz = f2_pack(jsm[6 * np + li], jsm[6 * np + li]);
+                if (DSW) {
+                    I.lx = f2_pack(jsm[7 * np + li], jsm[7 * np + li]);
+                    I.ly = f2_pack(jsm[8 * np + li], jsm[8 * np + li]);
+                    I.lz = f2_pack(jsm[9 * np + li], jsm[9 * np + li]);
+                }
+                float tot[6], lo[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) tot[c] = lo[c] = 0.0f;
+                // the row's T threads take groups of 4 j in turn (group g: j = 4 (g T + sub)),
+                // so the lanes of a warp read consecutive 16-byte words (no bank conflicts)
+                const int G = L / 4;
+                for (int g0 = 0; g0 < G; g0 += 32) {  // folds of 128 terms
+                    const int ge = min(g0 + 32, G);
+                    f2_t p[7];
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) p[c] = 0ull;
+#pragma unroll 2
+                    for (int g = g0; g < ge; ++g) {
+                        const int jj = (g * T + sub) * 4;
+                        f2_t v[NA][2];
+#pragma unroll
+                        for (int a = 0; a < NA; ++a) {
+                            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * np + jj]);
+                            v[a][0] = q.x;
+                            v[a][1] = q.y;
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            pair_term_x2<MODE, true>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
+                                                     DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
+                                                     DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, jj + 2 * h, gi, p);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
+                        float e, o;
+                        f2_unpack(p[c], e, o);
+                        const float part = e + o;
+                        if (DSW)
+                            fold_ds_rn(tot[c], lo[c], part);
+                        else
+                            tot[c] = __fadd_rn(tot[c], part);
+                    }
+                }
+                // the T sums of a row: a butterfly within the warp, then warp by warp
+                for (int o = 1; o < TW; o <<= 1) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float h2 = __shfl_xor_sync(0xffffffffu, tot[c], o);
+                        if (DSW) {
+                            const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
+                            ds_merge(tot[c], lo[c], h2, l2);
+                        } else {
+                            tot[c] = __fadd_rn(tot[c], h2);
+                        }
+                    }
+                }
+                if (T > 32) {
+                    if (lane == 0)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {
+                            wred[warp][c][0] = tot[c];
+                            wred[warp][c][1] = lo[c];
+                        }
+                    __syncthreads();
+                    if (sub == 0)
+                        for (int w = warp + 1; w < warp + T / 32; ++w)
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) {
+                                if (DSW)
+                                    ds_merge(tot[c], lo[c], wred[w][c][0], wred[w][c][1]);
+                                else
+                                    tot[c] = __fadd_rn(tot[c], wred[w][c][0]);
+                            }
+                }
+                if (live && sub == 0)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        f_hi[rr][c] = tot[c];
+                        f_lo[rr][c] = DSW ? lo[c] : 0.0f;
+                    }
+                __syncthreads();  // wred and the sums of this pass are done
+            }
+            // the corrector (FP64): up to 8 rows in one warp with 4 lanes per row (lanes 0-2
+            // one component each, then the four norms of Eq. (timestep) one per lane: the
+            // same operations as correct_row, in parallel); more rows one per lane, in as
+            // few warps as possible
+            if (cnt <= 8) {
+                if (warp == 0) {
+                    const int q = lane >> 2, part = lane & 3, base = lane & ~3;
+                    const bool live = q < cnt;
+                    const int r = row_idx[live ? q : 0];
+                    double f[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        f[c] = DSW ? f2d(f_hi[live ? q : 0][c]) + f2d(f_lo[live ? q : 0][c])
+                                   : f2d(f_hi[live ? q : 0][c]);
+                    const CorrDt d = corr_dt(static_cast<int64_t>(tb) - ld_state<true>(S.t + r), A.tick, A.lmax);
+                    double a2e = 0.0, a3 = 0.0;
+                    bool finite = true;
+                    if (part < 3) {
+                        const double fa = part == 0 ? f[0] : part == 1 ? f[1] : f[2];
+                        const double fk = part == 0 ? f[3] : part == 1 ? f[4] : f[5];
+                        double xn, vn;
+                        corr_dim(ld_state<true>(S.x[part] + r), ld_state<true>(S.v[part] + r),
+                                 ld_state<true>(S.a[part] + r), ld_state<true>(S.k[part] + r), fa, fk, d, xn, vn,
+                                 a2e, a3);
+                        finite = isfinite(xn) && isfinite(vn) && isfinite(fa) && isfinite(fk);
+                        if (live) {
+                            S.x[part][r] = xn;
+                            S.v[part][r] = vn;
+                            S.a[part][r] = fa;
+                            S.k[part][r] = fk;
+                        }
+                    }
+                    double u[3][2];  // a^(2) and a^(3) of the row, every component
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        u[c][0] = __shfl_sync(0xffffffffu, a2e, base + c);
+                        u[c][1] = __shfl_sync(0xffffffffu, a3, base + c);
+                    }
+                    // all four lanes' finiteness (every lane takes part in every shuffle)
+                    const int f1 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 1);
+                    const int f2 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 2);
+                    finite = finite && f1 && f2;
+                    const int f3 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 1);
+                    finite = finite && f3;
+                    double w[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        w[c] = part == 0 ? f[c] : part == 1 ? f[3 + c] : part == 2 ? u[c][0] : u[c][1];
+                    const double nrm = norm3(w);  // |ap|, |kp|, |a^(2)|, |a^(3)| on lanes 0-3
+                    const double an = __shfl_sync(0xffffffffu, nrm, base), kn = __shfl_sync(0xffffffffu, nrm, base + 1);
+                    const double a2n = __shfl_sync(0xffffffffu, nrm, base + 2);
+                    const double a3n = __shfl_sync(0xffffffffu, nrm, base + 3);
+                    if (live && part == 0) {
+                        const int l_new = corr_level(an, kn, a2n, a3n, A.eta, A.lmin, A.lmax,
+                                                     ld_state<true>(S.level + r), static_cast<int64_t>(tb), finite,
+                                                     A.st);
+                        S.t[r] = static_cast<int64_t>(tb);
+                        S.level[r] = static_cast<int8_t>(l_new);
+                        const unsigned long long dd = tb + (1ull << (A.lmax - l_new));
+                        due_r[q] = dd;
+                        const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
+                        *cl.map_shared_rank(&due_c[r - o * chunk], o) = dd;
+                    }
+                }
+            } else if (tid < cnt) {
+                double f[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    f[c] = DSW ? f2d(f_hi[tid][c]) + f2d(f_lo[tid][c]) : f2d(f_hi[tid][c]);
+                const int r = row_idx[tid];
+                const int l_new = correct_row<true>(S, r, f, f + 3, static_cast<int64_t>(tb), A.tick, A.eta, A.lmin,
+                                                    A.lmax, A.st);
+                const unsigned long long d = tb + (1ull << (A.lmax - l_new));
+                due_r[tid] = d;
+                const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
+                *cl.map_shared_rank(&due_c[r - o * chunk], o) = d;
+            }
+        }
+        cnt_last = cnt;
+        ++done;
+        rows += na;
+        last_t = static_cast<long long>(tb);
+    }
+    if (rank == 0 && tid == 0) {
+        A.sched_out->t_blk = static_cast<long long>(tb);
+        A.sched_out->n_act = na;
+        A.L->blocks = done;
+        A.L->rows = rows;
+        A.L->last_t = last_t;
+    }
+    cl.sync();  // no CTA leaves while another may still store into its shared memory
+}
+
+template <int MODE>
+int cluster_size_for()
+{
+    // 16 CTAs where the device takes that non-portable size, else the portable 8
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    auto kern = cluster_step_kernel<MODE>;
+    const size_t smem = static_cast<size_t>(SoaTile<MODE>::NA) * kClMaxPad * sizeof(float);
+    cached = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return cached;
+    }
+    for (int C : {16, 8}) {
+        if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1) {
+            cached = C;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return cached;
+}
+
+}  // namespace
+
+int cluster_step_size(int mode)
+{
+    if (mode == kModePlain) return cluster_size_for<kModePlain>();
+    if (mode == kModeComp) return cluster_size_for<kModeComp>();
+    return 0;
+}
+
+cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin,
+                                int lmax, long long t_end, long long budget, long long rows_max, long long last_t,
+                                unsigned stop_flags, DevStatus *st, SchedOut *sched_out, StepLoop *L,
+                                int32_t *act_out, int32_t *lists, cudaStream_t s, int64_t *launches)
+{
+    const int C = cluster_step_size(mode);
+    if (C == 0 || C > kClMaxC || J.n_pad > kClMaxPad || J.n_pad % kJTile != 0 || J.n_pad / C > kClMaxChunk || !J.soa)
+        return cudaErrorInvalidValue;
+    ClArgs A;
+    A.S = S;
+    A.soa = J.soa;
+    A.n_pad = J.n_pad;
+    A.eps2 = static_cast<float>(eps2);
+    A.tick = ldexp(1.0, -lmax);
+    A.eta = eta;
+    A.lmin = lmin;
+    A.lmax = lmax;
+    A.t_end = t_end;
+    A.budget = budget;
+    A.rows_max = rows_max;
+    A.last_t = last_t;
+    A.stop_flags = stop_flags;
+    A.st = st;
+    A.sched_out = sched_out;
+    A.L = L;
+    A.act_out = act_out;
+    A.lists = lists;
+    const int na_arr = mode == kModeComp ? SoaTile<kModeComp>::NA : SoaTile<kModePlain>::NA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(na_arr) * J.n_pad * sizeof(float);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = mode == kModeComp ? cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModeComp>, A)
+                                            : cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModePlain>, A);
+    if (e == cudaSuccess) ++*launches;
+    return e;
+}
+
+}  // namespace nb

@@ -139,7 +139,11 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
         // j-subgroup blocks are short: give each range 8, 4 or 2 tiles while the grid
         // still fills the GPU (8 only with six waves or more).  At N = 65536: 1024 and
         // 1594 rows fastest with 4 tiles (compensated 117 and 164 us, against 125 and 184
-        // with 2), 4096 rows with 8.
+        // with 2), 4096 rows with 8.  One wave of longer ranges (the balanced ranges allow
+        // any split) measured slower: 1024 rows compensated in 19 ranges of 13-14 tiles,
+        // one wave of 304 blocks, took 131 us against 114 with 4-tile ranges in 3.4
+        // waves; the block scheduler evening out SMs of unequal speed with many short
+        // blocks gains more than a full last wave.
         const int64_t slots = static_cast<int64_t>(sm_count) * std::max(1, occupancy(mode, threads, ipt));
         int t = 1;
         if (n_tiles >= 8 && static_cast<int64_t>(n_iblk) * (n_tiles / 8) >= 6 * slots) t = 8;
@@ -148,7 +152,7 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
         split = (n_tiles + t - 1) / t;
     }
     const int tps = (n_tiles + split - 1) / split;
-    split = (n_tiles + tps - 1) / tps;
+    split = (n_tiles + tps - 1) / tps;  // the fewest ranges of that length
     cfg->threads = threads;
     cfg->ipt = jsub ? 1 : ipt;
     cfg->jsub = jsub ? kJSub : 1;
@@ -204,7 +208,6 @@ cudaError_t force_launch(int mode, const JStream &js, int64_t n, const int32_t *
     P.n_act_dev = n_act_dev;
     P.n = static_cast<int>(n);
     P.n_tiles = static_cast<int>(js.n_pad / kJTile);
-    P.tiles_per_split = c.tiles_per_split;
     P.eps2 = eps2;
     P.acc = acc;
     P.jerk = jerk;

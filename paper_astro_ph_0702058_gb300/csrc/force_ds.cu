@@ -37,7 +37,7 @@ struct DsParams {
     const float4 *__restrict__ vel;    // (vx_hi, vy_hi, vz_hi, 0)
     const float4 *__restrict__ vello;  // (vx_lo, vy_lo, vz_lo, 0)
     const int32_t *__restrict__ active;
-    int n_act, n, n_tiles, tiles_per_split;
+    int n_act, n, n_tiles;
     ds eps2;
     double *__restrict__ acc, *__restrict__ jerk, *__restrict__ pot;
     float *__restrict__ part;  // [split][14][n_act] when split > 1
@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(kDsThreads) force_ds_kernel(const DsParams P)
 #pragma unroll
     for (int c = 0; c < 7; ++c) sum[c] = {0.0f, 0.0f};
 
-    const int t_begin = blockIdx.y * P.tiles_per_split;
-    const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
+    int t_begin, t_end;
+    jrange_tiles(blockIdx.y, gridDim.y, P.n_tiles, t_begin, t_end);
     for (int t = t_begin; t < t_end; ++t) {
         const size_t off = static_cast<size_t>(t) * kJTile;
         __syncthreads();
@@ -145,7 +145,6 @@ cudaError_t force_ds_launch(const JStream &js, int64_t n, const int32_t *active,
     P.n_act = static_cast<int>(n_act);
     P.n = static_cast<int>(n);
     P.n_tiles = static_cast<int>(js.n_pad / kJTile);
-    P.tiles_per_split = cfg.tiles_per_split;
     const float e_hi = static_cast<float>(eps2);
     P.eps2 = {e_hi, static_cast<float>(eps2 - static_cast<double>(e_hi))};
     P.acc = acc;

@@ -50,8 +50,7 @@ struct ForceParams {
     const long long *n_act_dev;  // when set, the block size is read here on the device (graph replays);
                                  // n_act then only bounds the launch
     int n;
-    int n_tiles;
-    int tiles_per_split;
+    int n_tiles;  // j-ranges: jrange_tiles over gridDim.y
     float eps2;
     double *__restrict__ acc;
     double *__restrict__ jerk;
@@ -227,8 +226,8 @@ __global__ void __launch_bounds__(NT) force_kernel(const ForceParams P)
     __shared__ __align__(8) uint64_t bar[2];
 
     const int tid = threadIdx.x;
-    const int t_begin = blockIdx.y * P.tiles_per_split;
-    const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
+    int t_begin, t_end;
+    jrange_tiles(blockIdx.y, gridDim.y, P.n_tiles, t_begin, t_end);
 
     float4 xi[IPT], vi[IPT], li[IPT];
     int gi[IPT];

@@ -326,8 +326,8 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     if (static_cast<int>(blockIdx.x) * RB * IPT >= n_act) return;  // a launch sized for more rows
     const int tid = threadIdx.x;
     const int row = tid % RB, sub = tid / RB;
-    const int t_begin = blockIdx.y * P.tiles_per_split;
-    const int t_end = min(t_begin + P.tiles_per_split, P.n_tiles);
+    int t_begin, t_end;
+    jrange_tiles(blockIdx.y, gridDim.y, P.n_tiles, t_begin, t_end);
     const f2_t E2 = f2_pack(P.eps2, P.eps2);
     const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
     const size_t n_pad = static_cast<size_t>(P.n_tiles) * kJTile;

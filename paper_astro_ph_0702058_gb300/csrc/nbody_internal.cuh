@@ -66,6 +66,14 @@ __device__ __forceinline__ bool nb_debug_check(const bool ok, DevStatus *st, con
 #define NB_CHECK(cond, st, site) true
 #endif
 
+// Tiles [b, e) of j-range r when n_tiles tiles are cut into `split` ranges whose lengths
+// differ by at most one tile (every force kernel: range r = blockIdx.y of split = gridDim.y).
+__host__ __device__ __forceinline__ void jrange_tiles(const int r, const int split, const int n_tiles, int &b, int &e)
+{
+    b = static_cast<int>(static_cast<long long>(r) * n_tiles / split);
+    e = static_cast<int>(static_cast<long long>(r + 1) * n_tiles / split);
+}
+
 // FP64 master state, structure of arrays: component c of particle i is x[c][i].
 struct State {
     int64_t n;
@@ -98,7 +106,7 @@ struct ForceConfig {
     int threads;          // threads per block
     int ipt;              // i-particles per thread
     int split;            // j-ranges (gridDim.y)
-    int tiles_per_split;  // tiles of kJTile j per range
+    int tiles_per_split;  // tiles of kJTile j in the longest range (lengths differ by at most one)
     int n_iblk;           // i-blocks (gridDim.x)
     int jsub = 1;         // threads per row, each taking 1/jsub of every tile (1 or 4)
 };
@@ -201,6 +209,22 @@ struct LoopArgs {
 // scheduler's kernel when it is one block, n <= 2048).
 cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, SchedOut *out, void *scratch,
                                  const LoopArgs &la, cudaStream_t s, int64_t *launches);
+
+// ---- cluster_step.cu ----
+// Block steps of systems of n_pad <= kClMaxPad inside one thread-block cluster
+// (16 CTAs where the device allows it, else 8), packed plain and compensated
+// modes.  One launch runs blocks while the next one is due by t_end, budget is
+// left, no flag of stop_flags is raised and its size is 1 .. rows_max; it writes
+// L->blocks, rows, last_t, the next block's time and size to sched_out and its
+// list to act_out (n ints); lists is scratch of n ints.
+constexpr int kClMaxPad = 4096;
+constexpr int kClMaxChunk = 512;  // particles per CTA (n_pad / cluster size)
+// The cluster size the mode's kernel launches with on this device, or 0 (no cluster launch).
+int cluster_step_size(int mode);
+cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin,
+                                int lmax, long long t_end, long long budget, long long rows_max, long long last_t,
+                                unsigned stop_flags, DevStatus *st, SchedOut *sched_out, StepLoop *L,
+                                int32_t *act_out, int32_t *lists, cudaStream_t s, int64_t *launches);
 
 // E_kin and E_pot (phi scratch: n doubles; out: 2 doubles); the potential in
 // FP64 or, with ds_potential, in double-single arithmetic (energy_ds.cu).

@@ -85,57 +85,81 @@ __device__ __forceinline__ int level_of(double dt, int lmin, int lmax, bool *cla
     return L;
 }
 
-// Corrector of Sect. 2 for particle i (its forces at the predicted state in
-// ap_in[3], kp_in[3]), then Eq. (timestep) and the new level; the step ends
-// at tick t_new.  Updates x, v, a, k, t, level of i.
-__device__ __forceinline__ void correct_row(const State &S, const int64_t i, const double *ap_in,
-                                            const double *kp_in, const int64_t t_new, const double tick,
-                                            const double eta, const int lmin, const int lmax, DevStatus *st)
+// State loads: through L2 only (CG, for state that another CTA of the same
+// launch may have written since this SM last read it) or plain.
+template <bool CG>
+__device__ __forceinline__ double ld_state(const double *p)
 {
-    const int64_t steps = t_new - S.t[i];
-    const double dt = static_cast<double>(steps) * tick;
+    if constexpr (CG) return __ldcg(p);
+    return *p;
+}
+template <bool CG>
+__device__ __forceinline__ int64_t ld_state(const int64_t *p)
+{
+    if constexpr (CG) return static_cast<int64_t>(__ldcg(reinterpret_cast<const long long *>(p)));
+    return *p;
+}
+template <bool CG>
+__device__ __forceinline__ int8_t ld_state(const int8_t *p)
+{
+    if constexpr (CG) return static_cast<int8_t>(__ldcg(reinterpret_cast<const signed char *>(p)));
+    return *p;
+}
+
+// Step quantities of the corrector of Sect. 2 for a step of `steps` ticks of
+// 2^-lmax: dt, 1/dt, 1/dt^2, dt^3, dt^4 and the predictor's factors.
+struct CorrDt {
+    double dt, idt, idt2, dt3, dt4;
+    PredDt pd;
+};
+__device__ __forceinline__ CorrDt corr_dt(const int64_t steps, const double tick, const int lmax)
+{
+    CorrDt d;
+    d.dt = static_cast<double>(steps) * tick;
     // 1/dt: when the step is 2^k ticks of 2^-lmax (every particle of a block) it
     // is 2^(lmax - k), built from its exponent bits; otherwise an IEEE division.
     // Both give the same bits.
-    const double idt = (steps > 0 && (steps & (steps - 1)) == 0)
-                           ? __longlong_as_double(static_cast<long long>(1023 + lmax - (__ffsll(steps) - 1)) << 52)
-                           : 1.0 / dt;
-    const double idt2 = idt * idt;
-    const double dt3 = dt * dt * dt;
-    const double dt4 = dt3 * dt;
-    double ap[3], kp[3], a2e[3], a3[3];
-    bool finite = true;
-    const PredDt pd = pred_dt(dt);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double a = S.a[c][i];
-        const double k = S.k[c][i];
-        double xp, vp;
-        predict_dim(S.x[c][i], S.v[c][i], a, k, pd, xp, vp);
-        ap[c] = ap_in[c];
-        kp[c] = kp_in[c];
-        const double da = a - ap[c];  // Delta a = a - a_p
-        const double a2 = -6.0 * da * idt2 - (4.0 * k + 2.0 * kp[c]) * idt;
-        a3[c] = 12.0 * da * idt2 * idt + 6.0 * (k + kp[c]) * idt2;
-        // the Taylor coefficients 1/24, 1/120, 1/6 as products (an FP64 division
-        // is a long dependent sequence on this part's narrow FP64 pipe)
-        const double xn = xp + dt4 * (a2 * (1.0 / 24.0) + a3[c] * dt * (1.0 / 120.0));
-        const double vn = vp + dt3 * (a2 * (1.0 / 6.0) + a3[c] * dt * (1.0 / 24.0));
-        a2e[c] = a2 + a3[c] * dt;  // a^(2) at the end of the step
-        finite = finite && isfinite(xn) && isfinite(vn) && isfinite(ap[c]) && isfinite(kp[c]);
-        S.x[c][i] = xn;
-        S.v[c][i] = vn;
-        S.a[c][i] = ap[c];
-        S.k[c][i] = kp[c];
-    }
-    // Eq. (timestep) with end-of-step quantities.
-    const double an = norm3(ap), kn = norm3(kp), a2n = norm3(a2e), a3n = norm3(a3);
+    d.idt = (steps > 0 && (steps & (steps - 1)) == 0)
+                ? __longlong_as_double(static_cast<long long>(1023 + lmax - (__ffsll(steps) - 1)) << 52)
+                : 1.0 / d.dt;
+    d.idt2 = d.idt * d.idt;
+    d.dt3 = d.dt * d.dt * d.dt;
+    d.dt4 = d.dt3 * d.dt;
+    d.pd = pred_dt(d.dt);
+    return d;
+}
+
+// One component of the corrector: from x, v, a, k at the start of the step and
+// the force ap, kp at the predicted state, the corrected xn, vn and a^(2), a^(3)
+// at the end of the step.
+__device__ __forceinline__ void corr_dim(const double x, const double v, const double a, const double k,
+                                         const double ap, const double kp, const CorrDt &d, double &xn,
+                                         double &vn, double &a2e, double &a3)
+{
+    double xp, vp;
+    predict_dim(x, v, a, k, d.pd, xp, vp);
+    const double da = a - ap;  // Delta a = a - a_p
+    const double a2 = -6.0 * da * d.idt2 - (4.0 * k + 2.0 * kp) * d.idt;
+    a3 = 12.0 * da * d.idt2 * d.idt + 6.0 * (k + kp) * d.idt2;
+    // the Taylor coefficients 1/24, 1/120, 1/6 as products (an FP64 division
+    // is a long dependent sequence on this part's narrow FP64 pipe)
+    xn = xp + d.dt4 * (a2 * (1.0 / 24.0) + a3 * d.dt * (1.0 / 120.0));
+    vn = vp + d.dt3 * (a2 * (1.0 / 6.0) + a3 * d.dt * (1.0 / 24.0));
+    a2e = a2 + a3 * d.dt;  // a^(2) at the end of the step
+}
+
+// Eq. (timestep) from |a|, |k|, |a^(2)|, |a^(3)| at the end of the step, then the
+// level rule: shrink at once, grow one level when the new time allows.  Raises
+// the non-finite and dt_min flags; returns the new level.
+__device__ __forceinline__ int corr_level(const double an, const double kn, const double a2n, const double a3n,
+                                          const double eta, const int lmin, const int lmax, const int l_old,
+                                          const int64_t t_new, const bool finite, DevStatus *st)
+{
     const double num = an * a2n + kn * kn;
     const double den = kn * a3n + a2n * a2n;
     const double dtc = den == 0.0 ? static_cast<double>(INFINITY) : sqrt(eta * num / den);
     bool clamped = false;
     const int lc = level_of(dtc, lmin, lmax, &clamped);
-    const int l_old = S.level[i];
     int l_new;
     if (!finite || lc < 0) {
         l_new = lmax;
@@ -152,8 +176,39 @@ __device__ __forceinline__ void correct_row(const State &S, const int64_t i, con
         atomicOr(&st->flags, kFlagDtMin);
         atomicAdd(&st->below_min, 1ull);
     }
+    return l_new;
+}
+
+// Corrector of Sect. 2 for particle i (its forces at the predicted state in
+// ap_in[3], kp_in[3]), then Eq. (timestep) and the new level; the step ends
+// at tick t_new.  Updates x, v, a, k, t, level of i and returns the new level.
+template <bool CG = false>
+__device__ __forceinline__ int correct_row(const State &S, const int64_t i, const double *ap_in,
+                                            const double *kp_in, const int64_t t_new, const double tick,
+                                            const double eta, const int lmin, const int lmax, DevStatus *st)
+{
+    const CorrDt d = corr_dt(t_new - ld_state<CG>(S.t + i), tick, lmax);
+    double ap[3], kp[3], a2e[3], a3[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ap[c] = ap_in[c];
+        kp[c] = kp_in[c];
+        double xn, vn;
+        corr_dim(ld_state<CG>(S.x[c] + i), ld_state<CG>(S.v[c] + i), ld_state<CG>(S.a[c] + i),
+                 ld_state<CG>(S.k[c] + i), ap[c], kp[c], d, xn, vn, a2e[c], a3[c]);
+        finite = finite && isfinite(xn) && isfinite(vn) && isfinite(ap[c]) && isfinite(kp[c]);
+        S.x[c][i] = xn;
+        S.v[c][i] = vn;
+        S.a[c][i] = ap[c];
+        S.k[c][i] = kp[c];
+    }
+    // Eq. (timestep) with end-of-step quantities.
+    const int l_new = corr_level(norm3(ap), norm3(kp), norm3(a2e), norm3(a3), eta, lmin, lmax,
+                                 ld_state<CG>(S.level + i), t_new, finite, st);
     S.t[i] = t_new;
     S.level[i] = static_cast<int8_t>(l_new);
+    return l_new;
 }
 
 // Block-wide reduction; `id` is the identity of `op` (pads missing warps).

@@ -36,14 +36,14 @@ for mode in ("plain", "comp", "sumcheck", "ds", "sorted"):
             out = (np.zeros((n_act, 3)), np.zeros((n_act, 3)), np.zeros(n_act))
             sim.force(act, acc=out[0], jerk=out[1], pot=out[2])
             assert np.isfinite(out[0]).all()
-for level in (2, 0):
+for level in (3, 2, 0):
     nbody_debug_step_graphs(level)
     for mode in ("plain", "comp"):
         m, x, v = plummer_sphere(1024, 1)
         with Simulation(m, x, v, EPS2, eta=0.01, mode=mode) as sim:
             sim.step(1.0 / 64)
             sim.energy(); sim.energy(ds_potential=True)
-nbody_debug_step_graphs(2)
+nbody_debug_step_graphs(3)
 m, x, v = plummer_sphere(20000, 2)
 with Simulation(m, x, v, EPS2, eta=0.02, mode="comp") as sim:
     sim.step(1.0 / 64)

@@ -27,7 +27,7 @@ def _run(m, x, v, mode, t_end, eta, graphs, max_steps=0):
             st = sim.stats()
             e = sum(sim.energy()) if max_steps == 0 else None  # energy needs synchronised particles
     finally:
-        nbody_debug_step_graphs(2)
+        nbody_debug_step_graphs(3)
     return nb, out, st, e
 
 
@@ -84,7 +84,7 @@ def test_device_loop_stops_at_the_strict_error_block(torch):
                 sim.get_state(**out)
                 res[level] = (sim.stats(), out)
         finally:
-            nbody_debug_step_graphs(2)
+            nbody_debug_step_graphs(3)
     (st0, s0), (st2, s2) = res[0], res[2]
     assert st0["blocks"] == st2["blocks"] and st0["below_dt_min"] == st2["below_dt_min"]
     assert st0["graph_blocks"] == 0 and st2["graph_blocks"] == st2["blocks"]
