@@ -926,8 +926,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
             const int64_t left = max_steps > 0 ? max_steps - done : kClusterCap;
             NB_CUDA(cluster_step_launch(c->p.mode, c->S, c->J, c->eps2, c->p.eta, c->p.lmin, c->p.lmax, tend,
                                         std::min(left, kClusterCap), c->n, c->t_pred, loop_stop_flags(c), c->st,
-                                        c->sched_out, c->loop_dev, c->act_sched, c->act_corr, c->s,
-                                        &c->stats.kernel_launches),
+                                        c->sched_out, c->loop_dev, c->act_sched, c->s, &c->stats.kernel_launches),
                     "cluster block-step launch");
             NB_CUDA(cudaMemcpyAsync(L, c->loop_dev, sizeof(StepLoop), cudaMemcpyDeviceToHost, c->s), "loop read-back");
             NB_CUDA(cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, c->s),

@@ -14,12 +14,13 @@
 //      the minimum, the block time (each CTA keeps the due ticks of its own
 //      particles in shared memory; a corrector stores a row's new one into its
 //      owner's);
-//   2. each CTA lists its active particles (ascending) in global memory,
-//      predicts all of its particles into the structure-of-arrays j-stream and
-//      stores its count into every CTA's shared memory; barrier C;
-//   3. the block's rows, in list order, are cut into C equal contiguous shares;
-//      each CTA copies the whole predicted j-stream into shared memory, computes
-//      the force on its share over all n j (T threads per row, T a power of
+//   2. each CTA predicts all of its particles into the structure-of-arrays
+//      j-stream in global memory and stores its active particles (ascending) and
+//      their count into every CTA's shared memory; barrier C;
+//   3. each CTA copies the predicted j-stream into shared memory (asynchronous
+//      copies through L2, while it finds its rows): the block's rows, in list
+//      order, cut into C equal contiguous shares.  It computes the force on its
+//      share over all n j (T threads per row, T a power of
 //      two, taking groups of 4 j in turn; the T sums added in a fixed tree), and
 //      corrects its share: up to 8 rows in one warp, 4 lanes per row, else one
 //      row per lane of as few warps as possible.
@@ -28,7 +29,8 @@
 // division or square root), so the FP64 corrector runs with 32 rows per warp
 // and the rows are spread evenly over the cluster's SMs; the predictor rounds
 // to float on the integer pipe (d2f_rn, f2d: the same bits).  State written by
-// one CTA and read by another in a later block is read through L2 only.
+// one CTA and read by another in a later block is read through L2 only.  The
+// masses of the j-stream are copied once.
 //
 // Every decision to go on or stop (block time past t_end, budget spent, a stop
 // flag, an empty block or one larger than rows_max) is taken from values every
@@ -71,7 +73,6 @@ struct ClArgs {
     SchedOut *sched_out;
     StepLoop *L;
     int32_t *act_out;  // the block's list (n), for the host
-    int32_t *lists;    // scratch (n): CTA r's active particles at r chunk ..
 };
 
 // Symmetric merge of two double-single sums (hi, lo) + (h2, l2): Knuth's
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     __shared__ float wred[kClWarps][6][2];
     __shared__ unsigned long long red_u64[32];
     __shared__ int b_pre[kClMaxC + 1];
+    __shared__ int lists[kClMaxPad];  // CTA r's active particles at r chunk .. (stored by CTA r)
     __shared__ unsigned long long due_c[kClMaxChunk];  // due ticks of this CTA's particles
     __shared__ unsigned long long due_r[kClMaxChunk];  // new due ticks of the rows it corrected last
 
@@ -121,6 +123,11 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     if (mine)
         due_c[tid] = static_cast<unsigned long long>(ld_state<true>(S.t + i) +
                                                      (int64_t(1) << (A.lmax - ld_state<true>(S.level + i))));
+    {  // the j-stream's masses (the rest is copied before each block's forces)
+        const float4 *src = reinterpret_cast<const float4 *>(A.soa + 3 * np);
+        float4 *dst = reinterpret_cast<float4 *>(jsm + 3 * np);
+        for (int k = tid; k < np / 4; k += kClThreads) dst[k] = src[k];
+    }
     cl.sync();  // every CTA of the cluster runs before any stores into another's shared memory
     long long done = 0, rows = 0, last_t = A.last_t;
     unsigned long long tb = 0;
@@ -163,49 +170,55 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                 before += k < warp ? warp_tot[k] : 0;
                 total += warp_tot[k];
             }
-            if (hit) A.lists[lo_i + before + __popc(mask & ((1u << lane) - 1u))] = i;
+            if (hit) {
+                const int slot = lo_i + before + __popc(mask & ((1u << lane) - 1u));
+                for (int r = 0; r < C; ++r) *cl.map_shared_rank(&lists[slot], r) = i;
+            }
             if (warp == 0 && lane < C) {
                 *cl.map_shared_rank(&x_cnt[rank], lane) = total;
                 if (rank == 0) *cl.map_shared_rank(&x_flags, lane) = x_flags;
             }
         }
-        cl.sync();  // barrier C: the lists and the j-stream are complete, the counts and flags stored
-        int pre = 0;
-        for (int r = 0; r < C; ++r) pre += x_cnt[r];
-        na = pre;
+        cl.sync();  // barrier C: the j-stream, the lists, the counts and the flags are stored
+        {  // the j-stream's positions and velocities into shared memory, while the rows are found
+            const int nq = np / 4;
+            for (int k = tid; k < (NA - 1) * nq; k += kClThreads) {
+                const int a = k / nq, off = 4 * (k - a * nq) + (a >= 3 ? a + 1 : a) * np;  // every array but m
+                cp_async16_cg(jsm + off, A.soa + off);
+            }
+            cp_async_commit();
+        }
+        if (warp == 0) {  // where each CTA's list starts in the block's list
+            const int v = lane < C ? x_cnt[lane] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane <= C) b_pre[lane] = incl - v;
+        }
+        __syncthreads();
+        na = b_pre[C];
         const bool go = done < A.budget && (x_flags & A.stop_flags) == 0u && static_cast<long long>(tb) <= A.t_end &&
                         na > 0 && na <= A.rows_max;
         // this CTA's share of the rows in list order, and the list for the host
         const int p0 = static_cast<int>(static_cast<long long>(rank) * na / C);
         const int p1 = static_cast<int>(static_cast<long long>(rank + 1) * na / C);
         const int cnt = p1 - p0;
-        if (tid == 0) {
-            int acc = 0;
-            for (int r = 0; r < C; ++r) {
-                b_pre[r] = acc;
-                acc += x_cnt[r];
-            }
-            b_pre[C] = acc;
-        }
-        __syncthreads();
         if (tid < cnt) {
             const int p = p0 + tid;
             int o = 0;
             while (o + 1 < C && b_pre[o + 1] <= p) ++o;
-            const int r = __ldcg(A.lists + o * chunk + (p - b_pre[o]));
+            const int r = lists[o * chunk + (p - b_pre[o])];
             row_idx[tid] = r;
             A.act_out[p] = r;
         }
+        cp_async_wait_all();
+        __syncthreads();
         if (!go) break;
 
-        // 3. the j-stream into shared memory (L2 reads: other CTAs wrote it)
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(A.soa);
-            float4 *dst = reinterpret_cast<float4 *>(jsm);
-            const int nv = NA * np / 4;
-            for (int k = tid; k < nv; k += kClThreads) dst[k] = __ldcg(src + k);
-        }
-        __syncthreads();
+        // 3. forces on this CTA's share of the rows, then their correction
         if (cnt > 0) {
             // T threads per row: the largest power of two with T cnt <= threads whose
             // j-share n_pad / T is a multiple of 8
@@ -218,6 +231,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                 const int rr = q0 + tid / T;
                 const int sub = tid % T;
                 const bool live = rr < cnt;
+                const bool warp_live = q0 + warp * 32 / T < cnt;  // a warp with no row skips the sums
                 const int gi = live ? row_idx[rr] : -1;
                 const int li = live ? gi : 0;
                 I2 I;
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                 for (int c = 0; c < 6; ++c) tot[c] = lo[c] = 0.0f;
                 // the row's T threads take groups of 4 j in turn (group g: j = 4 (g T + sub)),
                 // so the lanes of a warp read consecutive 16-byte words (no bank conflicts)
-                const int G = L / 4;
+                const int G = warp_live ? L / 4 : 0;
                 for (int g0 = 0; g0 < G; g0 += 32) {  // folds of 128 terms
                     const int ge = min(g0 + 32, G);
                     f2_t p[7];
@@ -271,7 +285,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                     }
                 }
                 // the T sums of a row: a butterfly within the warp, then warp by warp
-                for (int o = 1; o < TW; o <<= 1) {
+                for (int o = 1; o < (warp_live ? TW : 1); o <<= 1) {
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         const float h2 = __shfl_xor_sync(0xffffffffu, tot[c], o);
@@ -454,7 +468,7 @@ int cluster_step_size(int mode)
 cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin,
                                 int lmax, long long t_end, long long budget, long long rows_max, long long last_t,
                                 unsigned stop_flags, DevStatus *st, SchedOut *sched_out, StepLoop *L,
-                                int32_t *act_out, int32_t *lists, cudaStream_t s, int64_t *launches)
+                                int32_t *act_out, cudaStream_t s, int64_t *launches)
 {
     const int C = cluster_step_size(mode);
     if (C == 0 || C > kClMaxC || J.n_pad > kClMaxPad || J.n_pad % kJTile != 0 || J.n_pad / C > kClMaxChunk || !J.soa)
@@ -477,7 +491,6 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
     A.sched_out = sched_out;
     A.L = L;
     A.act_out = act_out;
-    A.lists = lists;
     const int na_arr = mode == kModeComp ? SoaTile<kModeComp>::NA : SoaTile<kModePlain>::NA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);

@@ -216,7 +216,7 @@ cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, Sche
 // modes.  One launch runs blocks while the next one is due by t_end, budget is
 // left, no flag of stop_flags is raised and its size is 1 .. rows_max; it writes
 // L->blocks, rows, last_t, the next block's time and size to sched_out and its
-// list to act_out (n ints); lists is scratch of n ints.
+// list to act_out (n ints).
 constexpr int kClMaxPad = 4096;
 constexpr int kClMaxChunk = 512;  // particles per CTA (n_pad / cluster size)
 // The cluster size the mode's kernel launches with on this device, or 0 (no cluster launch).
@@ -224,7 +224,7 @@ int cluster_step_size(int mode);
 cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin,
                                 int lmax, long long t_end, long long budget, long long rows_max, long long last_t,
                                 unsigned stop_flags, DevStatus *st, SchedOut *sched_out, StepLoop *L,
-                                int32_t *act_out, int32_t *lists, cudaStream_t s, int64_t *launches);
+                                int32_t *act_out, cudaStream_t s, int64_t *launches);
 
 // E_kin and E_pot (phi scratch: n doubles; out: 2 doubles); the potential in
 // FP64 or, with ds_potential, in double-single arithmetic (energy_ds.cu).

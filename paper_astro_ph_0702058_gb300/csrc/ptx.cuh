@@ -75,6 +75,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
         : "memory");
 }
 
+// 16-byte asynchronous copy from global to shared memory through L2 only
+// (cp.async.cg, the generic proxy: ordered by barriers like a load), then the
+// commit and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16_cg(void *dst_smem, const void *src_gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Approximate reciprocal square root on the MUFU unit.
 __device__ __forceinline__ float rsqrt_mufu(float x)
 {
