@@ -526,13 +526,13 @@ def c2_sweep(args):
 
 def c1_run(args):
     """C1: N = 1024 Plummer (seed 1), eps = 1/256, eta = 0.01, dt_max = 1/64, dt_min = 2^-26, from t = 0 to
-    1/8, in every force mode and in the FP64 oracle: blocks, wall time and |dE/E|."""
+    1/8, in every force mode and in the FP64 oracle: blocks, wall time and |dE/E| (--c1-n: other N)."""
     import torch
 
     import oracle
     from paper_astro_ph_0702058_gb300 import Simulation
     from synthetic import plummer_sphere
-    n, eps2, t_end = 1024, (1.0 / 256) ** 2, 0.125
+    n, eps2, t_end = args.c1_n, (1.0 / 256) ** 2, 0.125
     m, x, v = plummer_sphere(n, 1)
     torch.cuda.set_device(0)
     from paper_astro_ph_0702058_gb300 import nbody_debug_step_graphs
@@ -652,7 +652,9 @@ def diff_workload(args):
 
 def pipe_probe(args):
     """The roofline's unit rates, measured: FP32 FMA / ADD / MUL, packed FP32x2 FMA and MUFU rsqrt
-    results per SM per clock (csrc/pipe_probe.cu, chains of independent accumulators)."""
+    results per SM per clock (csrc/pipe_probe.cu, chains of independent accumulators), the FP64 FMA and
+    conversion rates, and the cycles per operation of one dependent FP64 chain (FMA, square root,
+    division) in one block of 1 to 16 warps."""
     from paper_astro_ph_0702058_gb300 import build as nb_build
     exe = nb_build.build_probe()
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
@@ -752,6 +754,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=None, help="--force-only: seed of the sphere (default 3)")
     ap.add_argument("--eps2", type=float, default=None, help="--force-only: softening squared (default 1e-6)")
     ap.add_argument("--c1-modes", default="plain,comp,sorted,ds", help="c1: the force modes to run")
+    ap.add_argument("--c1-n", type=int, default=1024, help="c1: particles (default 1024, the C1 configuration)")
     ap.add_argument("--step-graphs", type=int, default=3,
                     help="c1: 0 separate launches per block, 1 one graph replay per block, 2 the device-side loop, "
                          "3 the one-cluster block-step kernel")

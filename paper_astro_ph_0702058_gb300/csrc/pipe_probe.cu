@@ -1,7 +1,10 @@
 // Throughput probes of the GPU pipes that bound the pair loop: chains of
 // FP32 FMA, ADD and MUL, the packed FP32x2 FMA, and the MUFU reciprocal
 // square root; and of the pipes that bound the FP64 predictor and corrector:
-// FP64 FMA and the double -> float -> double conversions.  A standalone program (not part of libnbody.so); prints one
+// FP64 FMA and the double -> float -> double conversions.  Then the latency of
+// one dependent FP64 chain (FMA, square root + add, division + add) in one
+// block of 1, 4 or 16 warps with 1 or 32 active lanes: the cycles each
+// operation of a chain costs when the SM's FP64 unit is shared.  A standalone program (not part of libnbody.so); prints one
 // JSON line with results per SM and clock, the clock taken from clock64()
 // over the kernel's own duration.
 #include <cstdio>
@@ -113,6 +116,29 @@ __global__ void fp64_chain(float *out, long long *cyc, int iters, double a, doub
     if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - c0;
 }
 
+// One dependent chain per active lane (lanes < `lanes` of every warp); cycles per operation in cyc[0].
+template <int KIND>
+__global__ void fp64_dep(float *out, long long *cyc, int iters, int lanes, double a, double b)
+{
+    double r = 1.0 + threadIdx.x * 1e-3;
+    __syncthreads();
+    const long long c0 = clock64();
+    if (static_cast<int>(threadIdx.x & 31) < lanes) {
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < kInner; ++u) {
+                if (KIND == 0) r = fma(r, a, b);
+                else if (KIND == 1) r = sqrt(r) + b;
+                else r = b / r + a;
+            }
+        }
+    }
+    __syncthreads();
+    const long long c1 = clock64();
+    if (r == 12345.0) out[0] = 1.f;
+    if (threadIdx.x == 0) cyc[0] = c1 - c0;
+}
+
 }  // namespace
 
 int main()
@@ -159,6 +185,24 @@ int main()
     ops_per_thread = static_cast<double>(iters64) * kInner * kChains;
     run("dfma", 1.0, [&] { fp64_chain<0><<<blocks, threads>>>(out, cyc, iters64, 1.0000001, 1e-9); });
     run("f64_f32_f64_conversions", 2.0, [&] { fp64_chain<1><<<blocks, threads>>>(out, cyc, iters64, 0.0, 0.0); });
+    // dependent FP64 chains in one block: cycles per operation
+    const int dep_iters = 64;
+    auto dep = [&](const char *name, int warps, int lanes, auto launch) {
+        launch(warps, lanes);  // warm-up
+        launch(warps, lanes);
+        long long c = 0;
+        cudaMemcpy(&c, cyc, sizeof(long long), cudaMemcpyDeviceToHost);
+        std::printf("\"%s_%dw_%dl_clk_per_op\": %.1f, ", name, warps, lanes,
+                    static_cast<double>(c) / (dep_iters * kInner));
+    };
+    for (int wl : {1, 32, 4, 16}) {  // 1 warp with 1 or 32 lanes, 4 and 16 warps with 32 lanes
+        const int warps = wl == 32 ? 1 : wl, lanes = wl == 1 ? 1 : 32;
+        dep("dfma_dep", warps, lanes, [&](int w, int l) {
+            fp64_dep<0><<<1, 32 * w>>>(out, cyc, dep_iters, l, 1.0000001, 1e-9);
+        });
+    }
+    dep("dsqrt_plus_dadd_dep", 1, 32, [&](int w, int l) { fp64_dep<1><<<1, 32 * w>>>(out, cyc, dep_iters, l, 1.0, 1e-9); });
+    dep("ddiv_plus_dadd_dep", 1, 32, [&](int w, int l) { fp64_dep<2><<<1, 32 * w>>>(out, cyc, dep_iters, l, 1.0000001, 1e-9); });
     const cudaError_t err = cudaGetLastError();
     std::printf("\"sms\": %d, \"status\": \"%s\"}\n", sm, cudaGetErrorString(err));
     delete[] cyc_h;
