@@ -410,8 +410,8 @@ void nbody_ens_free(nbody_ens *e);
  *   acc, jerk (n_act x 3), pot (n_act): 8-byte aligned device doubles of the
  *     current device, written.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the scratch array: calls that
+ * (cudaGetSymbolAddress) with that device current.  All calls share the
+ * scratch array: calls that
  * overlap on the GPU race, so serialise them.  The call waits for its work
  * on `stream` and returns NBODY_EINVAL (bad argument; a host, misaligned or
  * other-device pointer; index out of range), NBODY_ETIMEOUT or NBODY_ECUDA;
