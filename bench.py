@@ -614,6 +614,50 @@ def block_run(args):
                       "rows": rows}), flush=True)
 
 
+# The paper's full-integration wall-clock over t = 0.25 -> 0.5 (Table 2, seconds), other hardware: context only.
+TABLE2_PAPER_S = {1024: {"GRAPE6Af": 0.3327, "8800GTX": 17.46, "FX1400": 20.20, "Xeon": 2.584},
+                  16384: {"GRAPE6Af": 16.32, "8800GTX": 924.4, "FX1400": 3398.0, "Xeon": 994.0},
+                  65536: {"GRAPE6Af": 178.2, "8800GTX": 3973.0, "FX1400": 40560.0, "Xeon": 19290.0},
+                  524288: {"8800GTX": 63960.0}}
+
+
+def table2_run(args):
+    """The paper's timed integration (Sect. 4, Table 2): an equal-mass Plummer sphere (seed 2), eps = 1/256,
+    eta = 0.01, dt_max = 1/8, dt_min = 2^-26, from t = 0 to 0.5, timed from t = 0.25 to 0.5 (wall clock around
+    nbody_step after a synchronised start), plain and compensated.  Reports blocks, pair interactions per second
+    and |dE/E| over the timed interval, with the paper's wall clock for the same N as context."""
+    import torch
+
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import plummer_sphere
+    torch.cuda.set_device(0)
+    eps2, eta = (1.0 / 256) ** 2, 0.01
+    out = []
+    for n in (int(v) for v in args.table2_n.split(",")):
+        m, x, v = plummer_sphere(n, 2)
+        rows = []
+        for mode in args.modes.split(","):
+            with Simulation(m, x, v, eps2, eta=eta, lmin=3, lmax=26, mode=mode) as sim:
+                sim.step(0.25)
+                sim.sync()
+                e0 = sum(sim.energy())
+                st0 = sim.stats()
+                t0 = time.perf_counter()
+                blocks = sim.step(0.5)
+                sim.sync()
+                wall = time.perf_counter() - t0
+                st = sim.stats()
+                e1 = sum(sim.energy())
+            pairs = st["pairs"] - st0["pairs"]
+            rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "pairs": int(pairs),
+                         "pairs_per_s": pairs / wall, "energy_error": abs((e1 - e0) / e0),
+                         "cluster_blocks": int(st["cluster_blocks"] - st0["cluster_blocks"])})
+        out.append({"n": n, "rows": rows, "paper_wall_s": TABLE2_PAPER_S.get(n)})
+    print(json.dumps({"workload": "table2", "eps2": eps2, "eta": eta, "dt_max": 0.125, "timed": [0.25, 0.5],
+                      "runs": out, "context": "paper Table 2: other hardware, FP32 on the GPUs; not a target"}),
+          flush=True)
+
+
 def diff_workload(args):
     """C5: loss and gradient of a shared-step Hermite rollout (N = 4096 Plummer, seed 5,
     eps = 1/128, 256 steps of 2^-9, checkpoints every 16 steps) through nbody_diff_rollout,
@@ -741,11 +785,13 @@ def main(argv=None):
     ap.add_argument("--force-only", action="store_true",
                     help="run one force call per mode on all N particles (for profilers), no timing")
     ap.add_argument("--modes", default="plain,comp")
-    ap.add_argument("--workload", choices=["c3", "ensemble", "c1", "c2-sweep", "c3-blocks", "c2-blocks", "diff", "pipe-probe"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "ensemble", "c1", "c2-sweep", "c3-blocks", "c2-blocks", "diff", "pipe-probe",
+                                           "table2"], default="c3",
                     help="c3: the headline full-force steps at N = 2^20; ensemble: the 512-cluster batched run; "
                          "c2-sweep: force-only rates against the block size at N = 65536; c3-blocks / c2-blocks: "
                          "free-running block steps at N = 2^20 to t = 1/64 / N = 65536 to t = 1; diff: rollout gradient (C5); "
-                         "pipe-probe: FP32 / FP32x2 / MUFU unit rates; c1: the C1 run in every mode and the oracle")
+                         "pipe-probe: FP32 / FP32x2 / MUFU unit rates; c1: the C1 run in every mode and the oracle; "
+                         "table2: the paper's timed integration (t = 0.25 to 0.5, eta = 0.01, dt_max = 1/8)")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--ens-sample", type=int, default=32,
                     help="clusters run one context each, for comparison (0: skip the comparison)")
@@ -759,6 +805,7 @@ def main(argv=None):
                     help="c1: 0 separate launches per block, 1 one graph replay per block, 2 the device-side loop, "
                          "3 the one-cluster block-step kernel")
     ap.add_argument("--t-end", type=float, default=None, help="c1: end time (a multiple of 1/64; default 1/8)")
+    ap.add_argument("--table2-n", default="1024,16384,65536", help="table2: particle numbers (524288 takes minutes)")
     args = ap.parse_args(argv)
     if args.force_only:
         force_only(args)
@@ -780,6 +827,9 @@ def main(argv=None):
         return
     if args.workload == "c1":
         c1_run(args)
+        return
+    if args.workload == "table2":
+        table2_run(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
