@@ -266,16 +266,17 @@ void nbody_debug_skip_tile_copy(int on);
  * the block time and size on the device):
  *   0  separate launches from the host for every block;
  *   1  one graph replay per block, then the host reads the next block back;
- *   2  (default) the block step is the body of a device-side loop (a while-node
+ *   2  the block step is the body of a device-side loop (a while-node
  *      of the graph): after each block's schedule one thread lets the next
  *      block run in the same replay while it is due by t_end, takes the
  *      graph's launch shape, no error flag is raised and the loop has added
  *      fewer than 1024 blocks to the replay's first; the host then reads back
  *      the next block.  Without while-nodes
  *      it acts as 1.
- *   3  (default) as 2, except that in the plain and compensated modes, with
- *      automatic force shapes (j_tile, i_block, j_split, j_sub all 0) and
- *      n_pad <= 4096, every block runs in one launch of a kernel of one
+ *   3  (default) as 2, except that in the plain and compensated modes with
+ *      n_pad <= 4096, and in the double-single mode with n_pad <= 2048, with
+ *      automatic force shapes (j_tile, i_block, j_split, j_sub all 0), every
+ *      block runs in one launch of a kernel of one
  *      thread-block cluster (16 or 8 CTAs) that repeats schedule, predictor,
  *      force and corrector on the device while the next block is due by
  *      t_end, no error flag is raised and max_steps allows (at most 4096

@@ -773,9 +773,11 @@ unsigned loop_stop_flags(const nbody_ctx *c)
 // Blocks of this context may run in the one-cluster kernel (level 3).
 bool cluster_steps(const nbody_ctx *c)
 {
-    if (g_step_graphs < 3 || (c->p.mode != NBODY_MODE_PLAIN && c->p.mode != NBODY_MODE_COMP)) return false;
+    const int mode = c->p.mode;
+    if (g_step_graphs < 3 || (mode != NBODY_MODE_PLAIN && mode != NBODY_MODE_COMP && mode != NBODY_MODE_DS))
+        return false;
     if (c->p.j_tile != 0 || c->p.i_block != 0 || c->p.j_split != 0 || c->p.j_sub != 0) return false;
-    if (!c->J.soa || c->n_pad > kClMaxPad) return false;
+    if (!c->J.soa || c->n_pad > (mode == NBODY_MODE_DS ? kClMaxPadDS : kClMaxPad)) return false;
     const int C = cluster_step_size(c->p.mode);
     return C > 0 && c->n_pad / C <= kClMaxChunk;
 }

@@ -41,11 +41,14 @@
 //
 // The pair term and its 128-term folds are those of the packed force kernel
 // (force_x2.cuh); the per-thread sums of a row are added in double-single
-// (compensated) or FP32 (plain) arithmetic in a fixed order.  The predictor and
+// (compensated) or FP32 (plain) arithmetic in a fixed order.  The double-single
+// mode (n_pad <= kClMaxPadDS) takes the pair term of force_ds.cu (ds_pair_term)
+// one j at a time over the float4 streams (x, m), (x_lo, m_lo), v, v_lo.  The predictor and
 // the corrector are those of step_impl.cuh, so the state a block leaves differs
 // from the separate kernels' only by the summation order of its forces.
 #include <cooperative_groups.h>
 
+#include "ds_arith.cuh"
 #include "force_x2.cuh"
 #include "step_impl.cuh"
 
@@ -63,8 +66,9 @@ static_assert(kClMaxChunk <= kClThreads, "one own particle per thread");
 struct ClArgs {
     State S;
     float *soa;  // the predicted j-stream (kSoaArrays x n_pad); padding entries stay as set up
+    float4 *posm, *poslo, *vel, *vello;  // its float4 form (double-single mode)
     int64_t n_pad;
-    float eps2;
+    float eps2, eps2_lo;  // eps^2 and, for the double-single mode, its low part
     double tick, eta;
     int lmin, lmax;
     long long t_end, budget, rows_max, last_t;
@@ -86,12 +90,22 @@ __device__ __forceinline__ void ds_merge(float &hi, float &lo, const float h2, c
     lo = __fadd_rn(__fadd_rn(lo, l2), e);
 }
 
+// Bytes of shared memory the mode's copy of the j-stream takes per particle.
+template <int MODE>
+constexpr int cl_jbytes()
+{
+    return MODE == kModeDS ? 4 * static_cast<int>(sizeof(float4)) : SoaTile<MODE>::NA * static_cast<int>(sizeof(float));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArgs A)
 {
+    constexpr bool DSM = MODE == kModeDS;
     constexpr int NA = SoaTile<MODE>::NA;
-    constexpr bool DSW = MODE == kModeComp;  // two-word sums
-    extern __shared__ __align__(16) float jsm[];  // NA x n_pad: the predicted j-stream
+    constexpr bool DSW = MODE == kModeComp || DSM;  // two-word sums
+    // the predicted j-stream: NA x n_pad floats (structure of arrays), or in the
+    // double-single mode 4 x n_pad float4: (x, m), (x_lo, m_lo), v, v_lo
+    extern __shared__ __align__(16) float jsm[];
     __shared__ unsigned long long x_min[kClMaxC];  // earliest due tick of each CTA (stored by that CTA)
     __shared__ int x_cnt[kClMaxC];                 // active count of each CTA (stored by that CTA)
     __shared__ unsigned x_flags;                   // status flags of this block (stored by CTA 0)
@@ -123,7 +137,14 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     if (mine)
         due_c[tid] = static_cast<unsigned long long>(ld_state<true>(S.t + i) +
                                                      (int64_t(1) << (A.lmax - ld_state<true>(S.level + i))));
-    {  // the j-stream's masses (the rest is copied before each block's forces)
+    float m_hi = 0.0f, m_lo = 0.0f;  // double-single mode: this thread's mass split
+    if constexpr (DSM) {
+        if (mine) {
+            const double mm = S.m[i];
+            m_hi = d2f_rn(mm);
+            m_lo = d2f_rn(mm - f2d(m_hi));
+        }
+    } else {  // the j-stream's masses (the rest is copied before each block's forces)
         const float4 *src = reinterpret_cast<const float4 *>(A.soa + 3 * np);
         float4 *dst = reinterpret_cast<float4 *>(jsm + 3 * np);
         for (int k = tid; k < np / 4; k += kClThreads) dst[k] = src[k];
@@ -152,16 +173,30 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
             if (lane == 0) warp_tot[warp] = __popc(mask);
             if (mine) {  // the state through L2: another CTA may have corrected it
                 const PredDt pd = pred_dt(static_cast<double>(static_cast<int64_t>(tb) - ld_state<true>(S.t + i)) * A.tick);
-                float *a = A.soa + i;
+                float h[3], hl[3], hv[3], hvl[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     double xp, vp;
                     predict_dim(ld_state<true>(S.x[c] + i), ld_state<true>(S.v[c] + i), ld_state<true>(S.a[c] + i),
                                 ld_state<true>(S.k[c] + i), pd, xp, vp);
-                    const float h = d2f_rn(xp);
-                    a[c * np] = h;
-                    a[(4 + c) * np] = d2f_rn(vp);
-                    if (DSW) a[(7 + c) * np] = d2f_rn(xp - f2d(h));  // the difference is exact
+                    h[c] = d2f_rn(xp);
+                    hv[c] = d2f_rn(vp);
+                    hl[c] = DSW ? d2f_rn(xp - f2d(h[c])) : 0.0f;  // the differences are exact
+                    hvl[c] = DSM ? d2f_rn(vp - f2d(hv[c])) : 0.0f;
+                }
+                if constexpr (DSM) {
+                    A.posm[i] = make_float4(h[0], h[1], h[2], m_hi);
+                    A.poslo[i] = make_float4(hl[0], hl[1], hl[2], m_lo);
+                    A.vel[i] = make_float4(hv[0], hv[1], hv[2], 0.0f);
+                    A.vello[i] = make_float4(hvl[0], hvl[1], hvl[2], 0.0f);
+                } else {
+                    float *a = A.soa + i;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        a[c * np] = h[c];
+                        a[(4 + c) * np] = hv[c];
+                        if (DSW) a[(7 + c) * np] = hl[c];
+                    }
                 }
             }
             __syncthreads();
@@ -180,7 +215,15 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
             }
         }
         cl.sync();  // barrier C: the j-stream, the lists, the counts and the flags are stored
-        {  // the j-stream's positions and velocities into shared memory, while the rows are found
+        if constexpr (DSM) {  // the four float4 streams into shared memory, while the rows are found
+            float4 *dst = reinterpret_cast<float4 *>(jsm);
+            const float4 *srcs[4] = {A.posm, A.poslo, A.vel, A.vello};
+            for (int k = tid; k < 4 * np; k += kClThreads) {
+                const int a = k / np, e = k - a * np;
+                cp_async16_cg(dst + k, srcs[a] + e);
+            }
+            cp_async_commit();
+        } else {  // the j-stream's positions and velocities into shared memory, while the rows are found
             const int nq = np / 4;
             for (int k = tid; k < (NA - 1) * nq; k += kClThreads) {
                 const int a = k / nq, off = 4 * (k - a * nq) + (a >= 3 ? a + 1 : a) * np;  // every array but m
@@ -234,54 +277,79 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                 const bool warp_live = q0 + warp * 32 / T < cnt;  // a warp with no row skips the sums
                 const int gi = live ? row_idx[rr] : -1;
                 const int li = live ? gi : 0;
-                I2 I;
-                I.x = f2_pack(jsm[li], jsm[li]);
-                I.y = f2_pack(jsm[np + li], jsm[np + li]);
-                I.z = f2_pack(jsm[2 * np + li], jsm[2 * np + li]);
-                I.vx = f2_pack(jsm[4 * np + li], jsm[4 * np + li]);
-                I.vy = f2_pack(jsm[5 * np + li], jsm[5 * np + li]);
-                I.vz = f2_pack(jsm[6 * np + li], jsm[6 * np + li]);
-                if (DSW) {
-                    I.lx = f2_pack(jsm[7 * np + li], jsm[7 * np + li]);
-                    I.ly = f2_pack(jsm[8 * np + li], jsm[8 * np + li]);
-                    I.lz = f2_pack(jsm[9 * np + li], jsm[9 * np + li]);
-                }
                 float tot[6], lo[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) tot[c] = lo[c] = 0.0f;
-                // the row's T threads take groups of 4 j in turn (group g: j = 4 (g T + sub)),
-                // so the lanes of a warp read consecutive 16-byte words (no bank conflicts)
-                const int G = warp_live ? L / 4 : 0;
-                for (int g0 = 0; g0 < G; g0 += 32) {  // folds of 128 terms
-                    const int ge = min(g0 + 32, G);
-                    f2_t p[7];
+                if constexpr (DSM) {
+                    // double-single pair terms, one j at a time: the row's T threads take j in turn
+                    const float4 *sp = reinterpret_cast<const float4 *>(jsm);
+                    const float4 ph = sp[li], pl = sp[np + li], vh = sp[2 * np + li], vl = sp[3 * np + li];
+                    const dsa::ds xi[3] = {{ph.x, pl.x}, {ph.y, pl.y}, {ph.z, pl.z}};
+                    const dsa::ds vi[3] = {{vh.x, vl.x}, {vh.y, vl.y}, {vh.z, vl.z}};
+                    const float e_hi = A.eps2;
+                    const dsa::ds e2 = {e_hi, A.eps2_lo};
+                    dsa::ds sum[7];
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) p[c] = 0ull;
-#pragma unroll 2
-                    for (int g = g0; g < ge; ++g) {
-                        const int jj = (g * T + sub) * 4;
-                        f2_t v[NA][2];
-#pragma unroll
-                        for (int a = 0; a < NA; ++a) {
-                            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * np + jj]);
-                            v[a][0] = q.x;
-                            v[a][1] = q.y;
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; ++h)
-                            pair_term_x2<MODE, true>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
-                                                     DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
-                                                     DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, jj + 2 * h, gi, p);
+                    for (int c = 0; c < 7; ++c) sum[c] = {0.0f, 0.0f};
+                    const int Lj = warp_live ? L : 0;
+#pragma unroll 1
+                    for (int g = 0; g < Lj; ++g) {
+                        const int j = g * T + sub;
+                        if (j == gi) continue;  // j = i contributes nothing
+                        dsa::ds_pair_term(sp[j], sp[np + j], sp[2 * np + j], sp[3 * np + j], xi, vi, e2, sum);
                     }
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
-                        float e, o;
-                        f2_unpack(p[c], e, o);
-                        const float part = e + o;
-                        if (DSW)
-                            fold_ds_rn(tot[c], lo[c], part);
-                        else
-                            tot[c] = __fadd_rn(tot[c], part);
+                    for (int c = 0; c < 6; ++c) {
+                        tot[c] = sum[c].h;
+                        lo[c] = sum[c].l;
+                    }
+                } else {
+                    I2 I;
+                    I.x = f2_pack(jsm[li], jsm[li]);
+                    I.y = f2_pack(jsm[np + li], jsm[np + li]);
+                    I.z = f2_pack(jsm[2 * np + li], jsm[2 * np + li]);
+                    I.vx = f2_pack(jsm[4 * np + li], jsm[4 * np + li]);
+                    I.vy = f2_pack(jsm[5 * np + li], jsm[5 * np + li]);
+                    I.vz = f2_pack(jsm[6 * np + li], jsm[6 * np + li]);
+                    if (DSW) {
+                        I.lx = f2_pack(jsm[7 * np + li], jsm[7 * np + li]);
+                        I.ly = f2_pack(jsm[8 * np + li], jsm[8 * np + li]);
+                        I.lz = f2_pack(jsm[9 * np + li], jsm[9 * np + li]);
+                    }
+                    // the row's T threads take groups of 4 j in turn (group g: j = 4 (g T + sub)),
+                    // so the lanes of a warp read consecutive 16-byte words (no bank conflicts)
+                    const int G = warp_live ? L / 4 : 0;
+                    for (int g0 = 0; g0 < G; g0 += 32) {  // folds of 128 terms
+                        const int ge = min(g0 + 32, G);
+                        f2_t p[7];
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) p[c] = 0ull;
+#pragma unroll 2
+                        for (int g = g0; g < ge; ++g) {
+                            const int jj = (g * T + sub) * 4;
+                            f2_t v[NA][2];
+#pragma unroll
+                            for (int a = 0; a < NA; ++a) {
+                                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * np + jj]);
+                                v[a][0] = q.x;
+                                v[a][1] = q.y;
+                            }
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                pair_term_x2<MODE, true>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
+                                                         DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
+                                                         DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, jj + 2 * h, gi, p);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
+                            float e, o;
+                            f2_unpack(p[c], e, o);
+                            const float part = e + o;
+                            if (DSW)
+                                fold_ds_rn(tot[c], lo[c], part);
+                            else
+                                tot[c] = __fadd_rn(tot[c], part);
+                        }
                     }
                 }
                 // the T sums of a row: a butterfly within the warp, then warp by warp
@@ -416,6 +484,8 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     cl.sync();  // no CTA leaves while another may still store into its shared memory
 }
 
+int cl_max_pad(int mode) { return mode == kModeDS ? kClMaxPadDS : kClMaxPad; }
+
 template <int MODE>
 int cluster_size_for()
 {
@@ -423,7 +493,7 @@ int cluster_size_for()
     static int cached = -1;
     if (cached >= 0) return cached;
     auto kern = cluster_step_kernel<MODE>;
-    const size_t smem = static_cast<size_t>(SoaTile<MODE>::NA) * kClMaxPad * sizeof(float);
+    const size_t smem = static_cast<size_t>(cl_jbytes<MODE>()) * cl_max_pad(MODE);
     cached = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
         cudaSuccess) {
@@ -462,6 +532,7 @@ int cluster_step_size(int mode)
 {
     if (mode == kModePlain) return cluster_size_for<kModePlain>();
     if (mode == kModeComp) return cluster_size_for<kModeComp>();
+    if (mode == kModeDS) return cluster_size_for<kModeDS>();
     return 0;
 }
 
@@ -471,13 +542,19 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
                                 int32_t *act_out, cudaStream_t s, int64_t *launches)
 {
     const int C = cluster_step_size(mode);
-    if (C == 0 || C > kClMaxC || J.n_pad > kClMaxPad || J.n_pad % kJTile != 0 || J.n_pad / C > kClMaxChunk || !J.soa)
+    if (C == 0 || C > kClMaxC || J.n_pad > cl_max_pad(mode) || J.n_pad % kJTile != 0 || J.n_pad / C > kClMaxChunk ||
+        !J.soa)
         return cudaErrorInvalidValue;
     ClArgs A;
     A.S = S;
     A.soa = J.soa;
+    A.posm = J.posm;
+    A.poslo = J.poslo;
+    A.vel = J.vel;
+    A.vello = J.vello;
     A.n_pad = J.n_pad;
     A.eps2 = static_cast<float>(eps2);
+    A.eps2_lo = static_cast<float>(eps2 - static_cast<double>(A.eps2));
     A.tick = ldexp(1.0, -lmax);
     A.eta = eta;
     A.lmin = lmin;
@@ -491,11 +568,12 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
     A.sched_out = sched_out;
     A.L = L;
     A.act_out = act_out;
-    const int na_arr = mode == kModeComp ? SoaTile<kModeComp>::NA : SoaTile<kModePlain>::NA;
+    const int jbytes = mode == kModeDS ? cl_jbytes<kModeDS>() : mode == kModeComp ? cl_jbytes<kModeComp>()
+                                                                                 : cl_jbytes<kModePlain>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kClThreads);
-    cfg.dynamicSmemBytes = static_cast<size_t>(na_arr) * J.n_pad * sizeof(float);
+    cfg.dynamicSmemBytes = static_cast<size_t>(jbytes) * J.n_pad;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -504,8 +582,9 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = mode == kModeComp ? cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModeComp>, A)
-                                            : cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModePlain>, A);
+    const cudaError_t e = mode == kModeDS     ? cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModeDS>, A)
+                          : mode == kModeComp ? cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModeComp>, A)
+                                              : cudaLaunchKernelEx(&cfg, cluster_step_kernel<kModePlain>, A);
     if (e == cudaSuccess) ++*launches;
     return e;
 }

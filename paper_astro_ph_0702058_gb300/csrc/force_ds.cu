@@ -82,25 +82,7 @@ __global__ void __launch_bounds__(kDsThreads) force_ds_kernel(const DsParams P)
 #pragma unroll 1
         for (int jj = 0; jj < kJTile; ++jj) {
             if (j0 + jj == gi) continue;  // j = i contributes nothing
-            const float4 a = sp[jj], b = sl[jj], u = sv[jj], w4 = svl[jj];
-            const ds dx[3] = {ds_add({a.x, b.x}, ds_neg(xi[0])), ds_add({a.y, b.y}, ds_neg(xi[1])),
-                              ds_add({a.z, b.z}, ds_neg(xi[2]))};
-            const ds dv[3] = {ds_add({u.x, w4.x}, ds_neg(vi[0])), ds_add({u.y, w4.y}, ds_neg(vi[1])),
-                              ds_add({u.z, w4.z}, ds_neg(vi[2]))};
-            const ds r2 = ds_add(ds_add(ds_add(P.eps2, ds_mul(dx[0], dx[0])), ds_mul(dx[1], dx[1])),
-                                 ds_mul(dx[2], dx[2]));
-            const ds rinv = ds_rsqrt(r2);
-            const ds rinv2 = ds_mul(rinv, rinv);
-            const ds mr = ds_mul({a.w, b.w}, rinv);
-            const ds mr3 = ds_mul(mr, rinv2);
-            const ds xv = ds_add(ds_add(ds_mul(dx[0], dv[0]), ds_mul(dx[1], dv[1])), ds_mul(dx[2], dv[2]));
-            const ds w = ds_mul_f(ds_mul(xv, rinv2), 3.0f);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                sum[c] = ds_add(sum[c], ds_mul(mr3, dx[c]));
-                sum[3 + c] = ds_add(sum[3 + c], ds_mul(mr3, ds_add(dv[c], ds_neg(ds_mul(w, dx[c])))));
-            }
-            sum[6] = ds_add(sum[6], ds_neg(mr));
+            ds_pair_term(sp[jj], sl[jj], sv[jj], svl[jj], xi, vi, P.eps2, sum);
         }
     }
     if (q >= P.n_act) return;

@@ -212,13 +212,14 @@ cudaError_t schedule_loop_launch(const State &S, int lmax, int32_t *active, Sche
 
 // ---- cluster_step.cu ----
 // Block steps of systems of n_pad <= kClMaxPad inside one thread-block cluster
-// (16 CTAs where the device allows it, else 8), packed plain and compensated
-// modes.  One launch runs blocks while the next one is due by t_end, budget is
+// (16 CTAs where the device allows it, else 8): packed plain and compensated
+// modes, and the double-single mode for n_pad <= kClMaxPadDS.  One launch runs blocks while the next one is due by t_end, budget is
 // left, no flag of stop_flags is raised and its size is 1 .. rows_max; it writes
 // L->blocks, rows, last_t, the next block's time and size to sched_out and its
 // list to act_out (n ints).
 constexpr int kClMaxPad = 4096;
-constexpr int kClMaxChunk = 512;  // particles per CTA (n_pad / cluster size)
+constexpr int kClMaxPadDS = 2048;  // the double-single mode's copy of the j-stream takes 64 B per particle
+constexpr int kClMaxChunk = 512;   // particles per CTA (n_pad / cluster size)
 // The cluster size the mode's kernel launches with on this device, or 0 (no cluster launch).
 int cluster_step_size(int mode);
 cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin,
