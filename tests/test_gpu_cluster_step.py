@@ -140,12 +140,61 @@ def test_cluster_stops_at_the_strict_error_block(torch):
 
 
 @pytest.mark.parametrize("n,mode,kw", [(4097, "comp", {}), (1024, "comp", {"j_split": 1}),
-                                       (1024, "plain", {"j_tile": 64}), (1024, "ds", {}),
+                                       (1024, "plain", {"j_tile": 64}), (2049, "ds", {}),
                                        (1024, "sorted", {}), (1024, "sumcheck", {})])
 def test_cluster_kernel_not_taken_outside_its_scope(torch, n, mode, kw):
-    """n_pad > 4096, a fixed force shape, or a mode other than plain / compensated: the tiled kernels."""
+    """n_pad > 4096 (2048 double-single), a fixed force shape, or the sorted and summation-check modes:
+    the tiled kernels."""
     m, x, v = plummer_sphere(n, 2)
     with _sim(m, x, v, mode, 0.02, **kw) as sim:
         nb = sim.step(1.0 / 64)
         st = sim.stats()
     assert nb > 0 and st["cluster_blocks"] == 0
+
+
+@pytest.mark.parametrize("n,blocks", [(1024, 40), (1000, 15), (2048, 8)])
+def test_cluster_ds_blocks_against_the_oracle(torch, n, blocks):
+    """Double-single mode in the cluster kernel, one block per call: the list is the oracle scheduler's,
+    the forces the corrector used within 1e-10 of the oracle's (reading gamma), the corrected state and
+    levels the oracle corrector's given those forces."""
+    eta = 0.01
+    m, x, v = plummer_sphere(n, 3 + n % 5)
+    with _sim(m, x, v, "ds", eta) as sim:
+        g = _state(sim)
+        for b in range(blocks):
+            tick, act = oracle.schedule(g["t_tick"], g["level"], LMAX)
+            assert sim.step(1.0, 1) == 1 and sim.stats()["cluster_blocks"] == b + 1
+            g2 = _state(sim)
+            st = _oracle_from(g, m, eta)
+            xp, vp = st.predict(tick)
+            ra, rk, _ = oracle.force(m, xp, vp, EPS2, act)
+            acc, jerk = g2["a"][act], g2["k"][act]
+            for got, ref in ((acc, ra), (jerk, rk)):
+                r = np.linalg.norm(ref, axis=1)
+                rel = np.linalg.norm(got - ref, axis=1) / np.maximum(r, 1e-3 * np.sqrt(np.mean(r ** 2)))
+                assert rel.max() <= 1e-10, (b, rel.max())
+            st.correct(act, xp, vp, acc, jerk, tick)
+            assert np.array_equal(g2["level"], st.level) and np.array_equal(g2["t_tick"], st.t), b
+            assert np.abs(g2["x"] - st.x).max() <= 1e-13 * np.abs(st.x).max(), b
+            g = g2
+
+
+def test_cluster_ds_free_run_follows_the_oracle_100_blocks(torch):
+    """C1 (N = 1024, eta = 0.01): the double-single cluster kernel, run free one block per call, and the
+    free-running FP64 oracle take the same first 100 block steps: block times, lists and every particle's
+    new time and level (the integer time bins)."""
+    n, eta = 1024, 0.01
+    m, x, v = plummer_sphere(n, 1)
+    ref = oracle.State(m, x, v, EPS2, eta, lmin=LMIN, lmax=LMAX).init()
+    with _sim(m, x, v, "ds", eta) as sim:
+        g = _state(sim)
+        assert np.array_equal(g["level"], ref.level)
+        for b in range(100):
+            t_ref, act_ref, _, _, _, _ = ref.step()
+            assert sim.step(1.0, 1) == 1
+            g2 = _state(sim)
+            moved = np.nonzero(g2["t_tick"] != g["t_tick"])[0]
+            assert np.array_equal(moved, act_ref) and np.all(g2["t_tick"][moved] == t_ref), f"block {b}: lists"
+            assert np.array_equal(g2["level"], ref.level) and np.array_equal(g2["t_tick"], ref.t), f"block {b}: levels"
+            g = g2
+        assert sim.stats()["cluster_blocks"] == 100
