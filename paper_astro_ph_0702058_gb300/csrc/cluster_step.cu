@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
             }
             if (hit) {
                 const int slot = lo_i + before + __popc(mask & ((1u << lane) - 1u));
-                for (int r = 0; r < C; ++r) *cl.map_shared_rank(&lists[slot], r) = i;
+                if (NB_CHECK(slot < hi_i, A.st, 4))
+                    for (int r = 0; r < C; ++r) *cl.map_shared_rank(&lists[slot], r) = i;
             }
             if (warp == 0 && lane < C) {
                 *cl.map_shared_rank(&x_cnt[rank], lane) = total;
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
             const int p = p0 + tid;
             int o = 0;
             while (o + 1 < C && b_pre[o + 1] <= p) ++o;
-            const int r = lists[o * chunk + (p - b_pre[o])];
+            const int e = o * chunk + (p - b_pre[o]);
+            const int r = NB_CHECK(e >= o * chunk && e < min((o + 1) * chunk, np), A.st, 5) ? lists[e] : 0;
             row_idx[tid] = r;
             A.act_out[p] = r;
         }
@@ -452,7 +454,8 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                         const unsigned long long dd = tb + (1ull << (A.lmax - l_new));
                         due_r[q] = dd;
                         const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
-                        *cl.map_shared_rank(&due_c[r - o * chunk], o) = dd;
+                        if (NB_CHECK(o < C && r - o * chunk < chunk, A.st, 6))
+                            *cl.map_shared_rank(&due_c[r - o * chunk], o) = dd;
                     }
                 }
             } else if (tid < cnt) {
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                 const unsigned long long d = tb + (1ull << (A.lmax - l_new));
                 due_r[tid] = d;
                 const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
-                *cl.map_shared_rank(&due_c[r - o * chunk], o) = d;
+                if (NB_CHECK(o < C && r - o * chunk < chunk, A.st, 6)) *cl.map_shared_rank(&due_c[r - o * chunk], o) = d;
             }
         }
         cnt_last = cnt;

@@ -38,7 +38,7 @@ for mode in ("plain", "comp", "sumcheck", "ds", "sorted"):
             assert np.isfinite(out[0]).all()
 for level in (3, 2, 0):
     nbody_debug_step_graphs(level)
-    for mode in ("plain", "comp"):
+    for mode in ("plain", "comp", "ds"):
         m, x, v = plummer_sphere(1024, 1)
         with Simulation(m, x, v, EPS2, eta=0.01, mode=mode) as sim:
             sim.step(1.0 / 64)
