@@ -14,21 +14,23 @@
 //      the minimum, the block time (each CTA keeps the due ticks of its own
 //      particles in shared memory; a corrector stores a row's new one into its
 //      owner's);
-//   2. each CTA predicts all of its particles into the structure-of-arrays
-//      j-stream in global memory and stores its active particles (ascending) and
-//      their count into every CTA's shared memory; barrier C;
+//   2. each CTA predicts all of its particles into the j-stream in global
+//      memory (structure of arrays; the float4 streams in the double-single
+//      mode) and stores its active particles (ascending) and their count into
+//      every CTA's shared memory; barrier C;
 //   3. each CTA copies the predicted j-stream into shared memory (asynchronous
 //      copies through L2, while it finds its rows): the block's rows, in list
 //      order, cut into C equal contiguous shares.  It computes the force on its
-//      share over all n j (T threads per row, T a power of
-//      two, taking groups of 4 j in turn; the T sums added in a fixed tree), and
-//      corrects its share: up to 8 rows in one warp, 4 lanes per row, else one
-//      row per lane of as few warps as possible.
+//      share over all n j (T threads per row, T a power of two, taking groups of
+//      4 j in turn; the T sums added in a fixed tree), and corrects its share:
+//      up to 8 rows in one warp, 4 lanes per row, else one row per lane of as
+//      few warps as possible.
 // GB300's FP64 unit is one per SM and takes ~19 cycles per warp instruction
 // whatever the number of active lanes (64-cycle latency, ~650-700 for a
-// division or square root), so the FP64 corrector runs with 32 rows per warp
-// and the rows are spread evenly over the cluster's SMs; the predictor rounds
-// to float on the integer pipe (d2f_rn, f2d: the same bits).  State written by
+// division or square root), so the FP64 corrector packs its rows into as few
+// warps as the lanes allow, and the rows are spread evenly over the cluster's
+// SMs; the predictor rounds to float on the integer pipe (d2f_rn, f2d: the
+// same bits).  State written by
 // one CTA and read by another in a later block is read through L2 only.  The
 // masses of the j-stream are copied once.
 //
@@ -43,9 +45,10 @@
 // (force_x2.cuh); the per-thread sums of a row are added in double-single
 // (compensated) or FP32 (plain) arithmetic in a fixed order.  The double-single
 // mode (n_pad <= kClMaxPadDS) takes the pair term of force_ds.cu (ds_pair_term)
-// one j at a time over the float4 streams (x, m), (x_lo, m_lo), v, v_lo.  The predictor and
-// the corrector are those of step_impl.cuh, so the state a block leaves differs
-// from the separate kernels' only by the summation order of its forces.
+// one j at a time over the float4 streams (x, m), (x_lo, m_lo), v, v_lo.  The
+// predictor and the corrector are those of step_impl.cuh, so the state a block
+// leaves differs from the separate kernels' only by the summation order of its
+// forces.
 #include <cooperative_groups.h>
 
 #include "ds_arith.cuh"
