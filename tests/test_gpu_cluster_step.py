@@ -198,3 +198,29 @@ def test_cluster_ds_free_run_follows_the_oracle_100_blocks(torch):
             assert np.array_equal(g2["level"], ref.level) and np.array_equal(g2["t_tick"], ref.t), f"block {b}: levels"
             g = g2
         assert sim.stats()["cluster_blocks"] == 100
+
+
+@pytest.mark.parametrize("mode", ["plain", "comp", "ds"])
+def test_cluster_kepler_orbit_unsoftened(torch, mode):
+    """Two bodies on an e = 0.5 Kepler ellipse with eps = 0 (the self-term mask and the massless padding),
+    one period (t = 402/64 against 2 pi) through the cluster kernel: the same blocks as the FP64 oracle,
+    energy conserved to its level, and the final separation within the FP32 force noise of the oracle's."""
+    from paper_astro_ph_0702058_gb300 import Simulation
+    from synthetic import kepler_pair
+    m, x, v = kepler_pair(0.5)
+    t_end = 402 / 64
+    with Simulation(m, x, v, 0.0, eta=0.01, lmin=LMIN, lmax=LMAX, mode=mode) as sim:
+        e0 = sum(sim.energy())
+        nb = sim.step(t_end)
+        g = _state(sim)
+        e1 = sum(sim.energy())
+        st = sim.stats()
+    ref = oracle.State(m, x, v, 0.0, 0.01, lmin=LMIN, lmax=LMAX).init()
+    bt, _, _ = ref.evolve(int(t_end * 2 ** LMAX))
+    de, de_ref = abs(e1 / e0 - 1), abs(sum(ref.energy()) / e0 - 1)
+    sep, sep_ref = np.linalg.norm(g["x"][1] - g["x"][0]), np.linalg.norm(ref.x[1] - ref.x[0])
+    print(f"\n{mode}: blocks {nb} (oracle {len(bt)}), |dE/E| {de:.3e} (oracle {de_ref:.3e}), "
+          f"separation {sep:.12f} (oracle {sep_ref:.12f})")
+    assert st["cluster_blocks"] == nb and abs(nb - len(bt)) <= 2
+    assert abs(e0 + 0.125) < 1e-12 and de < 2 * de_ref + (1e-6 if mode == "plain" else 1e-8)
+    assert abs(sep - sep_ref) < (1e-4 if mode == "plain" else 1e-6)
