@@ -304,7 +304,8 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
     // float4 stream is staged and transposed (two barriers per tile).
     // JSUB > 1: a block holds NT / JSUB rows, each with JSUB threads that take
     // consecutive quarters (JSUB = 4) of every tile; at the end the JSUB sums of a
-    // row are added in shared memory in subgroup order (FP64).  The same rows
+    // row are added in shared memory in subgroup order (double-single, on the
+    // FP32 pipe: GB300's FP64 unit would take ~19 cycles per warp instruction).  The same rows
     // per block as JSUB = 1 with NT / JSUB threads, but blocks JSUB times shorter:
     // more, evenly filled waves for mid-size blocks, and each tile copy serves
     // JSUB times the pairs.
@@ -506,18 +507,26 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
         __syncthreads();
         const int q = blockIdx.x * RB + row;
         if (sub != 0 || q >= n_act) return;
-        double r[7];
+        float hs[7], ls[7];  // the JSUB sums as double-single pairs, added in subgroup order
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            double t = 0.0;
+            hs[c] = red[c * RB + row];
+            ls[c] = is_ds(MODE) ? red[(7 + c) * RB + row] : 0.0f;
 #pragma unroll
-            for (int g = 0; g < JSUB; ++g) {
-                t += static_cast<double>(red[(g * NCS + c) * RB + row]);
-                if (is_ds(MODE)) t += static_cast<double>(red[(g * NCS + 7 + c) * RB + row]);
+            for (int g = 1; g < JSUB; ++g) {
+                const float h2 = red[(g * NCS + c) * RB + row];
+                const float l2 = is_ds(MODE) ? red[(g * NCS + 7 + c) * RB + row] : 0.0f;
+                const float s = __fadd_rn(hs[c], h2);  // TwoSum of the high words, then the low words
+                const float bb = __fsub_rn(s, hs[c]);
+                const float e = __fadd_rn(__fsub_rn(hs[c], __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+                hs[c] = s;
+                ls[c] = __fadd_rn(__fadd_rn(ls[c], l2), e);
             }
-            r[c] = t;
         }
         if (gridDim.y == 1) {
+            double r[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) r[c] = static_cast<double>(hs[c]) + static_cast<double>(ls[c]);
             double *pa = P.acc + 3 * static_cast<size_t>(q);
             double *pk = P.jerk + 3 * static_cast<size_t>(q);
             pa[0] = r[0];
@@ -527,14 +536,17 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             pk[1] = r[4];
             pk[2] = r[5];
             P.pot[q] = r[6];
-        } else {  // a partial sum: (hi, lo) of the FP64 value, or its float
+        } else {  // a partial sum: the (hi, lo) pair, or in plain mode its rounded sum
             float *base = P.part + static_cast<size_t>(blockIdx.y) * NCS * n_act + q;
             if (!NB_CHECK(q < n_act, P.st, 2)) return;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
-                const float h = static_cast<float>(r[c]);
-                base[static_cast<size_t>(c) * n_act] = h;
-                if (is_ds(MODE)) base[static_cast<size_t>(7 + c) * n_act] = static_cast<float>(r[c] - static_cast<double>(h));
+                if (is_ds(MODE)) {
+                    base[static_cast<size_t>(c) * n_act] = hs[c];
+                    base[static_cast<size_t>(7 + c) * n_act] = ls[c];
+                } else {
+                    base[static_cast<size_t>(c) * n_act] = __fadd_rn(hs[c], ls[c]);
+                }
             }
         }
         return;
