@@ -82,17 +82,6 @@ struct ClArgs {
     int32_t *act_out;  // the block's list (n), for the host
 };
 
-// Symmetric merge of two double-single sums (hi, lo) + (h2, l2): Knuth's
-// TwoSum of the high words, the low words and its error added after.
-__device__ __forceinline__ void ds_merge(float &hi, float &lo, const float h2, const float l2)
-{
-    const float s = __fadd_rn(hi, h2);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-    hi = s;
-    lo = __fadd_rn(__fadd_rn(lo, l2), e);
-}
-
 // Bytes of shared memory the mode's copy of the j-stream takes per particle.
 template <int MODE>
 constexpr int cl_jbytes()
@@ -364,7 +353,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
                         const float h2 = __shfl_xor_sync(0xffffffffu, tot[c], o);
                         if (DSW) {
                             const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
-                            ds_merge(tot[c], lo[c], h2, l2);
+                            ds2_add(tot[c], lo[c], h2, l2);
                         } else {
                             tot[c] = __fadd_rn(tot[c], h2);
                         }
@@ -383,7 +372,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
 #pragma unroll
                             for (int c = 0; c < 6; ++c) {
                                 if (DSW)
-                                    ds_merge(tot[c], lo[c], wred[w][c][0], wred[w][c][1]);
+                                    ds2_add(tot[c], lo[c], wred[w][c][0], wred[w][c][1]);
                                 else
                                     tot[c] = __fadd_rn(tot[c], wred[w][c][0]);
                             }

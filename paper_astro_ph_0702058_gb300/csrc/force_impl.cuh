@@ -122,6 +122,18 @@ __device__ __forceinline__ void fold_ds_rn(float &hi, float &lo, const float x)
     lo = __fadd_rn(lo, e);
 }
 
+// Adds the double-single sum (h2, l2) to (hi, lo): TwoSum of the high words,
+// then the low words and its error (symmetric in its two operands).  On the
+// FP32 pipe: GB300's FP64 unit takes ~19 cycles per warp instruction.
+__device__ __forceinline__ void ds2_add(float &hi, float &lo, const float h2, const float l2)
+{
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+}
+
 // Summation-check pair term: the compensated pair term with every operation
 // written as a round-to-nearest intrinsic in a fixed order and the correctly
 // rounded reciprocal square root, each of the 7 terms folded into (tot, lo)
@@ -372,11 +384,12 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
 
 // The same sums for many j-ranges: a block of 256 threads holds 8 consecutive
 // rows of one component and 32 lanes per row; lane w adds the ranges w, w + 32,
-// ... of its row (FP64, ascending), so a warp loads 8 consecutive floats (one
-// 32-byte sector) of each of 4 ranges, and a row's ranges are spread over 32
-// lanes.  The lane sums of a row are then added in lane order.  The order
-// depends on the split only, not on the number of rows a launch is sized for.
-// Grid: (ceil(n_act / 8), 7).
+// ... of its row (ascending), so a warp loads 8 consecutive floats (one 32-byte
+// sector) of each of 4 ranges, and a row's ranges are spread over 32 lanes.  The
+// lane sums of a row are then added in lane order.  The order depends on the
+// split only, not on the number of rows a launch is sized for.  The sums are
+// double-single pairs on the FP32 pipe (ds2_add, ~2^-48 relative per addition),
+// FP64 in the summation-check mode.  Grid: (ceil(n_act / 8), 7).
 template <int MODE, int R>
 __global__ void __launch_bounds__(256) reduce_partials_2d_kernel(const float *__restrict__ part, int split,
                                                                  int n_act, double *__restrict__ acc,
@@ -385,25 +398,45 @@ __global__ void __launch_bounds__(256) reduce_partials_2d_kernel(const float *__
 {
     constexpr int NC = (is_ds(MODE)) ? 14 : 7;
     constexpr int L = 256 / R;  // lanes per row
+    constexpr bool F64 = MODE == kModeCheck;
     __shared__ double sh[L][R];
+    __shared__ float shh[L][R], shl[L][R];
     if (n_act_dev) n_act = static_cast<int>(*n_act_dev);
     const int row = threadIdx.x % R, w = threadIdx.x / R;
     const int c = blockIdx.y;
     const int q = blockIdx.x * R + row;
     if (static_cast<int>(blockIdx.x) * R >= n_act) return;  // a launch sized for more rows
     double r = 0.0;
+    float rh = 0.0f, rl = 0.0f;
     if (q < n_act) {
         for (int sp = w; sp < split; sp += L) {
             const float *b = part + (static_cast<size_t>(sp) * NC + c) * n_act + q;
-            r += static_cast<double>(b[0]);
-            if (is_ds(MODE)) r += static_cast<double>(b[static_cast<size_t>(7) * n_act]);
+            const float l2 = is_ds(MODE) ? b[static_cast<size_t>(7) * n_act] : 0.0f;
+            if constexpr (F64) {
+                r += static_cast<double>(b[0]);
+                if (is_ds(MODE)) r += static_cast<double>(l2);
+            } else {
+                ds2_add(rh, rl, b[0], l2);
+            }
         }
     }
-    sh[w][row] = r;
+    if constexpr (F64) {
+        sh[w][row] = r;
+    } else {
+        shh[w][row] = rh;
+        shl[w][row] = rl;
+    }
     __syncthreads();
     if (w == 0 && q < n_act) {
-        double t = sh[0][row];
-        for (int k = 1; k < L; ++k) t += sh[k][row];
+        double t;
+        if constexpr (F64) {
+            t = sh[0][row];
+            for (int k = 1; k < L; ++k) t += sh[k][row];
+        } else {
+            float th = shh[0][row], tl = shl[0][row];
+            for (int k = 1; k < L; ++k) ds2_add(th, tl, shh[k][row], shl[k][row]);
+            t = static_cast<double>(th) + static_cast<double>(tl);
+        }
         if (c < 3)
             acc[3 * static_cast<size_t>(q) + c] = t;
         else if (c < 6)

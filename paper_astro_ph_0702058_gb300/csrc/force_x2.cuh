@@ -514,13 +514,8 @@ __global__ void NB_X2_BOUNDS(NT) force_kernel_x2(const ForceParams P)
             ls[c] = is_ds(MODE) ? red[(7 + c) * RB + row] : 0.0f;
 #pragma unroll
             for (int g = 1; g < JSUB; ++g) {
-                const float h2 = red[(g * NCS + c) * RB + row];
-                const float l2 = is_ds(MODE) ? red[(g * NCS + 7 + c) * RB + row] : 0.0f;
-                const float s = __fadd_rn(hs[c], h2);  // TwoSum of the high words, then the low words
-                const float bb = __fsub_rn(s, hs[c]);
-                const float e = __fadd_rn(__fsub_rn(hs[c], __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-                hs[c] = s;
-                ls[c] = __fadd_rn(__fadd_rn(ls[c], l2), e);
+                ds2_add(hs[c], ls[c], red[(g * NCS + c) * RB + row],
+                        is_ds(MODE) ? red[(g * NCS + 7 + c) * RB + row] : 0.0f);
             }
         }
         if (gridDim.y == 1) {
