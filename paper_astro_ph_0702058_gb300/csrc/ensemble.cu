@@ -392,20 +392,23 @@ __global__ void __launch_bounds__(NT) ens_force_kernel(const EnsDev E, const flo
     }
 }
 
-// Sums a row's j-range partials in ascending range order (FP64).
+// Sums a row's j-range partials in ascending range order, as double-single
+// pairs on the FP32 pipe (ds2_add; GB300's FP64 unit is narrow), then hi + lo in
+// FP64.  With one range the result is the range's hi + lo, as the
+// single-system kernel writes it.
 template <int NC>
 __device__ __forceinline__ void ens_row_sums(const EnsDev &E, long long r, int S, double (&f)[7])
 {
+    float h[7], l[7];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) f[k] = 0.0;
+    for (int k = 0; k < 7; ++k) h[k] = l[k] = 0.0f;
     for (int s = 0; s < S; ++s) {
         const float *base = E.part + ((static_cast<size_t>(r) * E.s_max) + s) * NC;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            f[k] += static_cast<double>(base[k]);
-            if (NC == 14) f[k] += static_cast<double>(base[7 + k]);
-        }
+        for (int k = 0; k < 7; ++k) ds2_add(h[k], l[k], base[k], NC == 14 ? base[7 + k] : 0.0f);
     }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) f[k] = static_cast<double>(h[k]) + static_cast<double>(l[k]);
 }
 
 __device__ __forceinline__ int ens_row_cluster(const EnsDev &E, long long r)
