@@ -484,41 +484,40 @@ int cl_max_pad(int mode) { return mode == kModeDS ? kClMaxPadDS : kClMaxPad; }
 template <int MODE>
 int cluster_size_for()
 {
-    // 16 CTAs where the device takes that non-portable size, else the portable 8
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    auto kern = cluster_step_kernel<MODE>;
-    const size_t smem = static_cast<size_t>(cl_jbytes<MODE>()) * cl_max_pad(MODE);
-    cached = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return cached;
-    }
-    for (int C : {16, 8}) {
-        if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    // 16 CTAs where the device takes that non-portable size, else the portable 8, else 0;
+    // found once per mode (a function-local static: thread-safe initialisation)
+    static const int size = [] {
+        auto kern = cluster_step_kernel<MODE>;
+        const size_t smem = static_cast<size_t>(cl_jbytes<MODE>()) * cl_max_pad(MODE);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess) {
             cudaGetLastError();
-            continue;
+            return 0;
         }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(C);
-        cfg.blockDim = dim3(kClThreads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = C;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1) {
-            cached = C;
-            break;
+        for (int C : {16, 8}) {
+            if (C > 8 &&
+                cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(kClThreads);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1) return C;
+            cudaGetLastError();
         }
-        cudaGetLastError();
-    }
-    return cached;
+        return 0;
+    }();
+    return size;
 }
 
 }  // namespace

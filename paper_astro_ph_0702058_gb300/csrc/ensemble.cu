@@ -568,12 +568,11 @@ void ens_force_instance(const EnsDev &E, float eps2, int grid, cudaStream_t s)
 template <int MODE, int NT, int IPT>
 int ens_force_occupancy()
 {
-    static int cached = -1;
-    if (cached < 0) {
+    static const int cached = [] {  // a function-local static: thread-safe initialisation
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_force_kernel<MODE, NT, IPT>, NT, 0);
-        cached = b;
-    }
+        return b;
+    }();
     return cached;
 }
 

@@ -1,4 +1,5 @@
 // Launch-shape choice and launch of the force evaluation (kernels in force_impl.cuh).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 
@@ -46,19 +47,19 @@ int shape_index(int threads, int ipt)
 // every device this library runs on is the same sm_103 part).
 int occupancy(int mode, int threads, int ipt)
 {
-    static int cache[5][11];
-    static bool filled[5][11];
+    static std::atomic<int> cache[5][11];  // resident blocks + 1; 0 until queried (host threads may race: same value)
     const int si = shape_index(threads, ipt);
     if (si < 0 || mode < 0 || mode > 4) return 0;
-    if (!filled[mode][si]) {
-        cache[mode][si] = mode == kModeComp    ? force_occupancy_comp(threads, ipt)
-                          : mode == kModeCheck ? force_occupancy_check(threads, ipt)
-                          : mode == kModeDS    ? force_occupancy_ds()
-                          : mode == kModeSorted ? 1
-                                               : force_occupancy_plain(threads, ipt);
-        filled[mode][si] = true;
+    int v = cache[mode][si].load(std::memory_order_acquire);
+    if (v == 0) {
+        v = 1 + (mode == kModeComp    ? force_occupancy_comp(threads, ipt)
+                 : mode == kModeCheck ? force_occupancy_check(threads, ipt)
+                 : mode == kModeDS    ? force_occupancy_ds()
+                 : mode == kModeSorted ? 1
+                                      : force_occupancy_plain(threads, ipt));
+        cache[mode][si].store(v, std::memory_order_release);
     }
-    return cache[mode][si];
+    return v - 1;
 }
 
 }  // namespace
