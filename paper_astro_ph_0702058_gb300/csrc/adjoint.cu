@@ -13,8 +13,7 @@
 // p both of its roles combine linearly: with G_a = m_p g_a,q - m_q g_a,p and
 // G_k likewise, one evaluation per pair (p, q) gives p's position and
 // velocity gradients.
-#include "nbody_internal.cuh"
-#include "ptx.cuh"
+#include "force_impl.cuh"  // fold_ds_rn; nbody_internal.cuh, ptx.cuh
 
 namespace nb {
 
@@ -37,7 +36,9 @@ __global__ void __launch_bounds__(kVjpThreads)
     const int pl = p < n ? p : 0;
     const float4 xi = posm[pl], vi = vel[pl], ga = gA[pl], gk = gK[pl];
     const float mp = xi.w;
-    double tx[3] = {0, 0, 0}, tv[3] = {0, 0, 0}, tm = 0.0;
+    // running totals over the tiles as double-single pairs on the FP32 pipe (fold_ds_rn;
+    // GB300's FP64 unit takes ~19 cycles per warp instruction), hi + lo in FP64 at the end
+    float hx[3] = {0, 0, 0}, lx[3] = {0, 0, 0}, hv[3] = {0, 0, 0}, lv[3] = {0, 0, 0}, hm = 0.f, lm = 0.f;
     const int j_begin = blockIdx.y * tiles_per_range * kVjpTile;
     const int j_end = min(j_begin + tiles_per_range * kVjpTile, n_pad);
     for (int j0 = j_begin; j0 < j_end; j0 += kVjpTile) {
@@ -84,12 +85,19 @@ __global__ void __launch_bounds__(kVjpThreads)
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            tx[c] += px[c];
-            tv[c] += pv[c];
+            fold_ds_rn(hx[c], lx[c], px[c]);
+            fold_ds_rn(hv[c], lv[c], pv[c]);
         }
-        tm += pm;
+        fold_ds_rn(hm, lm, pm);
     }
     if (p >= n) return;
+    double tx[3], tv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        tx[c] = static_cast<double>(hx[c]) + static_cast<double>(lx[c]);
+        tv[c] = static_cast<double>(hv[c]) + static_cast<double>(lv[c]);
+    }
+    const double tm = static_cast<double>(hm) + static_cast<double>(lm);
     if (gridDim.y == 1) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
