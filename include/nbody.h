@@ -237,6 +237,7 @@ typedef struct {
     int64_t loop_blocks;   /* of those, the ones the device-side loop added (no host round trip) */
     int last_j_sub;        /* threads per row of the last force kernel (1 or 4)    */
     int64_t cluster_blocks; /* block steps nbody_step ran in the one-cluster kernel */
+    int64_t grid_blocks;   /* block steps nbody_step ran in the whole-GPU cooperative kernel */
 } nbody_stats;
 
 int nbody_get_stats(nbody_ctx *ctx, nbody_stats *s);
@@ -280,8 +281,14 @@ void nbody_debug_skip_tile_copy(int on);
  *      thread-block cluster (16 or 8 CTAs) that repeats schedule, predictor,
  *      force and corrector on the device while the next block is due by
  *      t_end, no error flag is raised and max_steps allows (at most 4096
- *      blocks per launch).  Its forces are the same pair terms summed in
- *      another order, so its results differ from levels 0-2 in the last bits.
+ *      blocks per launch).  Larger plain and compensated systems (n up to
+ *      3584 per SM, automatic shapes) run their blocks of up to 4095 rows in
+ *      one cooperative launch of one CTA per SM that repeats the same steps,
+ *      its CTAs meeting at three grid barriers per block (each gives up after
+ *      about 1 s and raises NBODY_ETIMEOUT); a larger block ends the launch
+ *      and runs as at level 2.  Both kernels' forces are the same pair terms
+ *      summed in another order, so their results differ from levels 0-2 in
+ *      the last bits.
  * A context captures its graph in the form of the level in force when it
  * builds it (once, and again only if its scratch buffer moves); a loop graph
  * run at level 1 stops after each block.

@@ -57,7 +57,7 @@ class nbody_stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("last_threads", C.c_int), ("last_i_per_thread", C.c_int),
                 ("last_j_split", C.c_int), ("mode", C.c_int), ("graph_blocks", C.c_int64),
                 ("loop_blocks", C.c_int64), ("last_j_sub", C.c_int),
-                ("cluster_blocks", C.c_int64)]
+                ("cluster_blocks", C.c_int64), ("grid_blocks", C.c_int64)]
 
 
 class NBodyError(RuntimeError):
@@ -290,7 +290,9 @@ def nbody_debug_skip_tile_copy(on: bool) -> None:
 
 def nbody_debug_step_graphs(level: int) -> None:
     """0: separate launches, 1: one graph replay per block, 2: device-side block loop, 3 (default): as 2, and
-    the one-cluster block-step kernel for small plain and compensated systems (n_pad <= 4096)."""
+    the one-cluster block-step kernel for small systems (plain and compensated n_pad <= 4096, double-single
+    n_pad <= 2048), the whole-GPU cooperative kernel for the blocks of up to 4095 rows of larger plain and
+    compensated systems."""
     lib().nbody_debug_step_graphs(int(level))
 
 

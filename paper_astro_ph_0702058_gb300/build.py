@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnbody.so")
-SOURCES = ["api.cu", "force.cu", "force_plain.cu", "force_comp.cu", "force_check.cu", "force_sorted.cu", "force_ds.cu", "energy_ds.cu", "integrator.cu", "cluster_step.cu", "noalloc.cu", "ensemble.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "force.cu", "force_plain.cu", "force_comp.cu", "force_check.cu", "force_sorted.cu", "force_ds.cu", "energy_ds.cu", "integrator.cu", "cluster_step.cu", "grid_step.cu", "noalloc.cu", "ensemble.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-source nvcc flags (none at present).
 SOURCE_FLAGS: dict[str, list[str]] = {}

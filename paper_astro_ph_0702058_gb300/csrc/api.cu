@@ -24,7 +24,11 @@ int g_fail_alloc = 0;    // allocation-failure injection countdown (test hook)
 // replay per block, 2 a device-side loop of blocks in each replay
 int g_step_graphs = 3;
 constexpr int64_t kLoopCap = 1024;  // blocks one replay of the loop may run
-constexpr int64_t kClusterCap = 4096;  // blocks one launch of the cluster kernel may run
+constexpr int64_t kClusterCap = 4096;  // blocks one launch of the cluster or the grid kernel may run
+#ifndef NB_GRID_ROWS
+#define NB_GRID_ROWS 4095
+#endif
+constexpr int kGridRows = NB_GRID_ROWS;  // largest block the whole-GPU block-step kernel runs
 
 int fail(int code, const char *fmt, ...)
 {
@@ -126,6 +130,8 @@ struct nbody_ctx {
     unsigned char *graph_fits = nullptr;  // graph_rows + 1 flags: block size na takes the graph's shape
     StepLoop *loop_dev = nullptr;
     StepLoop *loop_host = nullptr;
+    void *grid_buf = nullptr;  // scratch of the whole-GPU block-step kernel (grid_step_bytes)
+    int grid_rows = 0;         // largest block it runs
     bool pred_valid = false;
     int64_t force_n_act = -1;
     int fused_split = 0;  // > 1: the last force left its j-range partials for the corrector
@@ -139,7 +145,7 @@ void release(nbody_ctx *c)
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     void *dev[] = {c->state, c->t, c->level, c->jbuf, c->act_force, c->act_corr, c->act_sched,
                    c->f_acc, c->f_jerk, c->f_pot, c->stage, c->partials, c->sched_scratch,
-                   c->sched_out, c->st, c->phi, c->e_out, c->trange, c->graph_fits, c->loop_dev};
+                   c->sched_out, c->st, c->phi, c->e_out, c->trange, c->graph_fits, c->loop_dev, c->grid_buf};
     for (void *d : dev)
         if (d) cudaFree(d);
     void *host[] = {c->sched_host, c->st_host, c->e_host, c->trange_host, c->loop_host};
@@ -782,6 +788,18 @@ bool cluster_steps(const nbody_ctx *c)
     return C > 0 && c->n_pad / C <= kClMaxChunk;
 }
 
+// Blocks of up to kGridRows rows of this context may run in the whole-GPU
+// cooperative kernel (level 3, plain and compensated systems past the cluster
+// kernel's sizes, n <= CTAs x kGrMaxChunk).
+bool grid_steps(const nbody_ctx *c)
+{
+    const int mode = c->p.mode;
+    if (g_step_graphs < 3 || (mode != NBODY_MODE_PLAIN && mode != NBODY_MODE_COMP)) return false;
+    if (c->p.j_tile != 0 || c->p.i_block != 0 || c->p.j_split != 0 || c->p.j_sub != 0) return false;
+    if (!c->J.soa || cluster_steps(c)) return false;
+    return grid_step_chunk(c->n, grid_step_size(mode)) > 0;
+}
+
 // Builds the replayed graph: the block step as the body of a while-node, whose
 // last kernel decides whether the next block runs in the same replay, then the
 // read-back of the next block, the status and the loop control.  Without
@@ -922,6 +940,13 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     r = schedule_internal(c, &tb, &na);
     const bool cluster = cluster_steps(c);
     bool cluster_declined = false;  // the cluster kernel ran none of the blocks it was offered
+    const bool grid = !cluster && grid_steps(c);
+    bool grid_declined = false;  // likewise the whole-GPU kernel
+    if (grid && !c->grid_buf) {
+        c->grid_rows = static_cast<int>(std::min<int64_t>(kGridRows, c->n));
+        NB_CUDA(dev_alloc(&c->grid_buf, grid_step_bytes(c->p.mode, c->grid_rows, grid_step_size(c->p.mode))),
+                "grid block-step scratch allocation");
+    }
     while (r == NBODY_OK && tb <= tend && !(max_steps > 0 && done >= max_steps)) {
         if (cluster && !cluster_declined) {
             StepLoop *L = c->loop_host;
@@ -955,9 +980,44 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
             cluster_declined = blocks == 0;  // that block takes the path below once
             continue;
         }
+        if (grid && !grid_declined && na <= c->grid_rows) {
+            StepLoop *L = c->loop_host;
+            const int64_t left = max_steps > 0 ? max_steps - done : kClusterCap;
+            NB_CUDA(grid_step_launch(c->p.mode, c->S, c->J, c->eps2, c->p.eta, c->p.lmin, c->p.lmax, tend,
+                                     std::min(left, kClusterCap), c->grid_rows, c->t_pred, loop_stop_flags(c), c->st,
+                                     c->sched_out, c->loop_dev, c->act_sched, c->grid_buf, c->s,
+                                     &c->stats.kernel_launches),
+                    "grid block-step launch");
+            NB_CUDA(cudaMemcpyAsync(L, c->loop_dev, sizeof(StepLoop), cudaMemcpyDeviceToHost, c->s), "loop read-back");
+            NB_CUDA(cudaMemcpyAsync(c->sched_host, c->sched_out, sizeof(SchedOut), cudaMemcpyDeviceToHost, c->s),
+                    "schedule read-back");
+            NB_CUDA(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->s),
+                    "status read-back");
+            NB_CUDA(cudaStreamSynchronize(c->s), "stream synchronise");
+            const int64_t blocks = L->blocks;
+            c->stats.force_calls += blocks;
+            c->stats.pairs += L->rows * (c->n - 1);
+            c->stats.blocks += blocks;
+            c->stats.grid_blocks += blocks;
+            if (blocks > 0) {
+                c->t_max = std::max(c->t_max, static_cast<int64_t>(L->last_t));
+                c->t_pred = L->last_t;
+                c->pred_valid = false;
+                c->force_n_act = -1;
+            }
+            done += blocks;
+            r = absorb_status(c);
+            if (r != NBODY_OK) break;
+            tb = c->sched_host->t_blk;
+            na = c->sched_host->n_act;
+            grid_declined = blocks == 0;  // that block takes the path below once
+            continue;
+        }
         cluster_declined = false;
+        grid_declined = false;
         ForceConfig cfg{};
-        bool use_graph = g_step_graphs > 0 && packed && c->graph_rows > 0 && na <= c->graph_rows &&
+        // (not beside the grid kernel: the graph's device loop would go on with the small blocks that follow)
+        bool use_graph = !grid && g_step_graphs > 0 && packed && c->graph_rows > 0 && na <= c->graph_rows &&
                          force_choose(c->p.mode, na, c->n_pad, c->sm_count, c->p.j_tile, c->p.i_block,
                                       c->p.j_split, &cfg, c->p.j_sub) == NBODY_OK &&
                          same_shape(cfg, c->graph_cfg);

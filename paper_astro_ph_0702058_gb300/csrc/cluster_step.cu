@@ -51,9 +51,7 @@
 // forces.
 #include <cooperative_groups.h>
 
-#include "ds_arith.cuh"
-#include "force_x2.cuh"
-#include "step_impl.cuh"
+#include "block_rows.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -121,8 +119,6 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     const int chunk = np / C;
     const int lo_i = rank * chunk;
     const int hi_i = static_cast<int>(min(static_cast<int64_t>(lo_i + chunk), n));
-    const f2_t E2 = f2_pack(A.eps2, A.eps2);
-    const f2_t NEG3 = f2_pack(-3.0f, -3.0f);
 
     const int i = lo_i + tid;  // this thread's own particle
     const bool mine = tid < chunk && i < hi_i;
@@ -261,208 +257,51 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
             // j-share n_pad / T is a multiple of 8
             int T = kClThreads;
             while (T > 1 && (T * cnt > kClThreads || (np / 8) % T != 0)) T >>= 1;
-            const int rpp = kClThreads / T;
-            const int L = np / T;
-            const int TW = T < 32 ? T : 32;
-            for (int q0 = 0; q0 < cnt; q0 += rpp) {
-                const int rr = q0 + tid / T;
-                const int sub = tid % T;
-                const bool live = rr < cnt;
-                const bool warp_live = q0 + warp * 32 / T < cnt;  // a warp with no row skips the sums
+            auto load_i = [&](const int rr, const bool live, I2 &I) {
                 const int gi = live ? row_idx[rr] : -1;
                 const int li = live ? gi : 0;
-                float tot[6], lo[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) tot[c] = lo[c] = 0.0f;
-                if constexpr (DSM) {
-                    // double-single pair terms, one j at a time: the row's T threads take j in turn
-                    const float4 *sp = reinterpret_cast<const float4 *>(jsm);
-                    const float4 ph = sp[li], pl = sp[np + li], vh = sp[2 * np + li], vl = sp[3 * np + li];
-                    const dsa::ds xi[3] = {{ph.x, pl.x}, {ph.y, pl.y}, {ph.z, pl.z}};
-                    const dsa::ds vi[3] = {{vh.x, vl.x}, {vh.y, vl.y}, {vh.z, vl.z}};
-                    const float e_hi = A.eps2;
-                    const dsa::ds e2 = {e_hi, A.eps2_lo};
-                    dsa::ds sum[7];
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) sum[c] = {0.0f, 0.0f};
-                    const int Lj = warp_live ? L : 0;
-#pragma unroll 1
-                    for (int g = 0; g < Lj; ++g) {
-                        const int j = g * T + sub;
-                        if (j == gi) continue;  // j = i contributes nothing
-                        dsa::ds_pair_term(sp[j], sp[np + j], sp[2 * np + j], sp[3 * np + j], xi, vi, e2, sum);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        tot[c] = sum[c].h;
-                        lo[c] = sum[c].l;
-                    }
-                } else {
-                    I2 I;
-                    I.x = f2_pack(jsm[li], jsm[li]);
-                    I.y = f2_pack(jsm[np + li], jsm[np + li]);
-                    I.z = f2_pack(jsm[2 * np + li], jsm[2 * np + li]);
-                    I.vx = f2_pack(jsm[4 * np + li], jsm[4 * np + li]);
-                    I.vy = f2_pack(jsm[5 * np + li], jsm[5 * np + li]);
-                    I.vz = f2_pack(jsm[6 * np + li], jsm[6 * np + li]);
-                    if (DSW) {
-                        I.lx = f2_pack(jsm[7 * np + li], jsm[7 * np + li]);
-                        I.ly = f2_pack(jsm[8 * np + li], jsm[8 * np + li]);
-                        I.lz = f2_pack(jsm[9 * np + li], jsm[9 * np + li]);
-                    }
-                    // the row's T threads take groups of 4 j in turn (group g: j = 4 (g T + sub)),
-                    // so the lanes of a warp read consecutive 16-byte words (no bank conflicts)
-                    const int G = warp_live ? L / 4 : 0;
-                    for (int g0 = 0; g0 < G; g0 += 32) {  // folds of 128 terms
-                        const int ge = min(g0 + 32, G);
-                        f2_t p[7];
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) p[c] = 0ull;
-#pragma unroll 2
-                        for (int g = g0; g < ge; ++g) {
-                            const int jj = (g * T + sub) * 4;
-                            f2_t v[NA][2];
-#pragma unroll
-                            for (int a = 0; a < NA; ++a) {
-                                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * np + jj]);
-                                v[a][0] = q.x;
-                                v[a][1] = q.y;
-                            }
-#pragma unroll
-                            for (int h = 0; h < 2; ++h)
-                                pair_term_x2<MODE, true>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
-                                                         DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
-                                                         DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, jj + 2 * h, gi, p);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
-                            float e, o;
-                            f2_unpack(p[c], e, o);
-                            const float part = e + o;
-                            if (DSW)
-                                fold_ds_rn(tot[c], lo[c], part);
-                            else
-                                tot[c] = __fadd_rn(tot[c], part);
-                        }
-                    }
+                I.x = f2_pack(jsm[li], jsm[li]);
+                I.y = f2_pack(jsm[np + li], jsm[np + li]);
+                I.z = f2_pack(jsm[2 * np + li], jsm[2 * np + li]);
+                I.vx = f2_pack(jsm[4 * np + li], jsm[4 * np + li]);
+                I.vy = f2_pack(jsm[5 * np + li], jsm[5 * np + li]);
+                I.vz = f2_pack(jsm[6 * np + li], jsm[6 * np + li]);
+                if (DSW && !DSM) {
+                    I.lx = f2_pack(jsm[7 * np + li], jsm[7 * np + li]);
+                    I.ly = f2_pack(jsm[8 * np + li], jsm[8 * np + li]);
+                    I.lz = f2_pack(jsm[9 * np + li], jsm[9 * np + li]);
                 }
-                // the T sums of a row: a butterfly within the warp, then warp by warp
-                for (int o = 1; o < (warp_live ? TW : 1); o <<= 1) {
+                return gi;
+            };
+            auto load_ds = [&](const int rr, const bool live, dsa::ds (&xi)[3], dsa::ds (&vi)[3]) {
+                const int gi = live ? row_idx[rr] : -1;
+                const int li = live ? gi : 0;
+                const float4 *sp = reinterpret_cast<const float4 *>(jsm);
+                const float4 ph = sp[li], pl = sp[np + li], vh = sp[2 * np + li], vl = sp[3 * np + li];
+                xi[0] = {ph.x, pl.x};
+                xi[1] = {ph.y, pl.y};
+                xi[2] = {ph.z, pl.z};
+                vi[0] = {vh.x, vl.x};
+                vi[1] = {vh.y, vl.y};
+                vi[2] = {vh.z, vl.z};
+                return gi;
+            };
+            auto store = [&](const int rr, const float *tot, const float *lo) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float h2 = __shfl_xor_sync(0xffffffffu, tot[c], o);
-                        if (DSW) {
-                            const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
-                            ds2_add(tot[c], lo[c], h2, l2);
-                        } else {
-                            tot[c] = __fadd_rn(tot[c], h2);
-                        }
-                    }
+                for (int c = 0; c < 6; ++c) {
+                    f_hi[rr][c] = tot[c];
+                    f_lo[rr][c] = DSW ? lo[c] : 0.0f;
                 }
-                if (T > 32) {
-                    if (lane == 0)
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) {
-                            wred[warp][c][0] = tot[c];
-                            wred[warp][c][1] = lo[c];
-                        }
-                    __syncthreads();
-                    if (sub == 0)
-                        for (int w = warp + 1; w < warp + T / 32; ++w)
-#pragma unroll
-                            for (int c = 0; c < 6; ++c) {
-                                if (DSW)
-                                    ds2_add(tot[c], lo[c], wred[w][c][0], wred[w][c][1]);
-                                else
-                                    tot[c] = __fadd_rn(tot[c], wred[w][c][0]);
-                            }
-                }
-                if (live && sub == 0)
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        f_hi[rr][c] = tot[c];
-                        f_lo[rr][c] = DSW ? lo[c] : 0.0f;
-                    }
-                __syncthreads();  // wred and the sums of this pass are done
-            }
-            // the corrector (FP64): up to 8 rows in one warp with 4 lanes per row (lanes 0-2
-            // one component each, then the four norms of Eq. (timestep) one per lane: the
-            // same operations as correct_row, in parallel); more rows one per lane, in as
-            // few warps as possible
-            if (cnt <= 8) {
-                if (warp == 0) {
-                    const int q = lane >> 2, part = lane & 3, base = lane & ~3;
-                    const bool live = q < cnt;
-                    const int r = row_idx[live ? q : 0];
-                    double f[6];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c)
-                        f[c] = DSW ? f2d(f_hi[live ? q : 0][c]) + f2d(f_lo[live ? q : 0][c])
-                                   : f2d(f_hi[live ? q : 0][c]);
-                    const CorrDt d = corr_dt(static_cast<int64_t>(tb) - ld_state<true>(S.t + r), A.tick, A.lmax);
-                    double a2e = 0.0, a3 = 0.0;
-                    bool finite = true;
-                    if (part < 3) {
-                        const double fa = part == 0 ? f[0] : part == 1 ? f[1] : f[2];
-                        const double fk = part == 0 ? f[3] : part == 1 ? f[4] : f[5];
-                        double xn, vn;
-                        corr_dim(ld_state<true>(S.x[part] + r), ld_state<true>(S.v[part] + r),
-                                 ld_state<true>(S.a[part] + r), ld_state<true>(S.k[part] + r), fa, fk, d, xn, vn,
-                                 a2e, a3);
-                        finite = isfinite(xn) && isfinite(vn) && isfinite(fa) && isfinite(fk);
-                        if (live) {
-                            S.x[part][r] = xn;
-                            S.v[part][r] = vn;
-                            S.a[part][r] = fa;
-                            S.k[part][r] = fk;
-                        }
-                    }
-                    double u[3][2];  // a^(2) and a^(3) of the row, every component
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        u[c][0] = __shfl_sync(0xffffffffu, a2e, base + c);
-                        u[c][1] = __shfl_sync(0xffffffffu, a3, base + c);
-                    }
-                    // all four lanes' finiteness (every lane takes part in every shuffle)
-                    const int f1 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 1);
-                    const int f2 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 2);
-                    finite = finite && f1 && f2;
-                    const int f3 = __shfl_xor_sync(0xffffffffu, static_cast<int>(finite), 1);
-                    finite = finite && f3;
-                    double w[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        w[c] = part == 0 ? f[c] : part == 1 ? f[3 + c] : part == 2 ? u[c][0] : u[c][1];
-                    const double nrm = norm3(w);  // |ap|, |kp|, |a^(2)|, |a^(3)| on lanes 0-3
-                    const double an = __shfl_sync(0xffffffffu, nrm, base), kn = __shfl_sync(0xffffffffu, nrm, base + 1);
-                    const double a2n = __shfl_sync(0xffffffffu, nrm, base + 2);
-                    const double a3n = __shfl_sync(0xffffffffu, nrm, base + 3);
-                    if (live && part == 0) {
-                        const int l_new = corr_level(an, kn, a2n, a3n, A.eta, A.lmin, A.lmax,
-                                                     ld_state<true>(S.level + r), static_cast<int64_t>(tb), finite,
-                                                     A.st);
-                        S.t[r] = static_cast<int64_t>(tb);
-                        S.level[r] = static_cast<int8_t>(l_new);
-                        const unsigned long long dd = tb + (1ull << (A.lmax - l_new));
-                        due_r[q] = dd;
-                        const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
-                        if (NB_CHECK(o < C && r - o * chunk < chunk, A.st, 6))
-                            *cl.map_shared_rank(&due_c[r - o * chunk], o) = dd;
-                    }
-                }
-            } else if (tid < cnt) {
-                double f[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c)
-                    f[c] = DSW ? f2d(f_hi[tid][c]) + f2d(f_lo[tid][c]) : f2d(f_hi[tid][c]);
-                const int r = row_idx[tid];
-                const int l_new = correct_row<true>(S, r, f, f + 3, static_cast<int64_t>(tb), A.tick, A.eta, A.lmin,
-                                                    A.lmax, A.st);
-                const unsigned long long d = tb + (1ull << (A.lmax - l_new));
-                due_r[tid] = d;
-                const int o = r / chunk;  // the owner keeps it for its schedule after barrier A
-                if (NB_CHECK(o < C && r - o * chunk < chunk, A.st, 6)) *cl.map_shared_rank(&due_c[r - o * chunk], o) = d;
-            }
+            };
+            rows_force<MODE, kClThreads>(jsm, np, 0, np, cnt, T, A.eps2, A.eps2_lo, load_i, load_ds, store, wred);
+            // the new due tick of each row: kept for this CTA's next minimum and stored into
+            // the owner's shared memory for its schedule after barrier A
+            auto due = [&](const int q, const int r, const unsigned long long dd) {
+                due_r[q] = dd;
+                const int o = r / chunk;
+                if (NB_CHECK(o < C && r - o * chunk < chunk, A.st, 6)) *cl.map_shared_rank(&due_c[r - o * chunk], o) = dd;
+            };
+            rows_correct<DSW>(S, row_idx, f_hi, f_lo, cnt, tb, A.tick, A.eta, A.lmin, A.lmax, A.st, due);
         }
         cnt_last = cnt;
         ++done;

@@ -227,6 +227,22 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
                                 unsigned stop_flags, DevStatus *st, SchedOut *sched_out, StepLoop *L,
                                 int32_t *act_out, cudaStream_t s, int64_t *launches);
 
+// ---- grid_step.cu ----
+// Block steps of larger systems (n <= CTAs x kGrMaxChunk) as one cooperative
+// launch of one CTA per SM, packed plain and compensated modes, with the same
+// contract as cluster_step_launch; `buf` is grid_step_bytes(mode, rows_max,
+// grid_step_size(mode)) bytes of device scratch.
+constexpr int kGrMaxChunk = 3584;  // particles per CTA (their prediction is held in shared memory)
+// CTAs of the mode's launch on this device (one per SM), or 0 (no cooperative launch).
+int grid_step_size(int mode);
+// Particles per CTA for n (ceil(n / ctas) rounded up to 4), or 0 when above kGrMaxChunk.
+int grid_step_chunk(int64_t n, int ctas);
+size_t grid_step_bytes(int mode, int rows_max, int ctas);
+cudaError_t grid_step_launch(int mode, const State &S, const JStream &J, double eps2, double eta, int lmin, int lmax,
+                             long long t_end, long long budget, int rows_max, long long last_t, unsigned stop_flags,
+                             DevStatus *st, SchedOut *sched_out, StepLoop *L, int32_t *act_out, void *buf,
+                             cudaStream_t s, int64_t *launches);
+
 // E_kin and E_pot (phi scratch: n doubles; out: 2 doubles); the potential in
 // FP64 or, with ds_potential, in double-single arithmetic (energy_ds.cu).
 cudaError_t energy_launch(const State &S, double eps2, double *phi_scratch, double *out,

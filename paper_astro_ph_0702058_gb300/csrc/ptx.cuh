@@ -1,5 +1,5 @@
 // Hand-written PTX wrappers: mbarriers, bulk (TMA) global->shared copies,
-// the MUFU reciprocal square root and the global timer.
+// the MUFU reciprocal square root, the global timer and a bounded grid barrier.
 #pragma once
 
 #include <cstdint>
@@ -61,6 +61,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if ((it & 63u) == 63u && global_timer_ns() - t0 > 2000000000ull) return false;
     }
     return false;
+}
+
+// Device-scope acquire load (pairs with the fence before an arrival).
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier of all CTAs of a cooperative launch (all co-resident): thread 0 of
+// each CTA fences the CTA's stores, adds 1 to *ctr (zero at launch) and waits
+// until it reaches `target` + CTAs (target: thread 0's count of arrivals
+// expected so far, advanced here).  Gives up after ~1 s of wall time and
+// returns false (the caller records a timeout); every thread of the CTA calls
+// it and gets the same answer through *s_ok.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *ctr, unsigned long long &target,
+                                             const unsigned ctas, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += ctas;
+        __threadfence();
+        atomicAdd(ctr, 1ull);
+        bool ok = false;
+        const uint64_t t0 = global_timer_ns();
+        for (uint32_t it = 0; it < (1u << 26); ++it) {
+            if (ld_acquire_gpu(ctr) >= target) {
+                ok = true;
+                break;
+            }
+            if ((it & 63u) == 63u && global_timer_ns() - t0 > 1000000000ull) break;
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 // One bulk asynchronous copy of `bytes` (multiple of 16, both addresses
