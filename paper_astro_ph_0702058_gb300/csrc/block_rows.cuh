@@ -10,10 +10,55 @@
 
 namespace nb {
 
+// One thread's part of a row in rows_force: the groups of 4 j (g T + sub) 4,
+// g < my, of the shared-memory copy, folded every 128 terms into (tot, lo).
+template <int MODE, bool SELF, int STRIDE>
+__device__ __forceinline__ void rows_sums_x2(const float *jsm, const int stride_rt, const int j0, const int my,
+                                             const int T, const int sub, const I2 &I, const int gi, const f2_t E2,
+                                             const f2_t NEG3, float (&tot)[6], float (&lo)[6])
+{
+    constexpr bool DSW = MODE == kModeComp;
+    constexpr int NA = SoaTile<MODE>::NA;
+    const int stride = STRIDE > 0 ? STRIDE : stride_rt;  // a compile-time stride folds into the load offsets
+    for (int g0 = 0; g0 < my; g0 += 32) {  // folds of 128 terms
+        const int ge = min(g0 + 32, my);
+        f2_t p[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) p[c] = 0ull;
+#pragma unroll 2
+        for (int g = g0; g < ge; ++g) {
+            const int jj = (g * T + sub) * 4;
+            f2_t v[NA][2];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * stride + jj]);
+                v[a][0] = q.x;
+                v[a][1] = q.y;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
+                                         DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
+                                         DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, j0 + jj + 2 * h, gi, p);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
+            float e, o;
+            f2_unpack(p[c], e, o);
+            const float part = e + o;
+            if (DSW)
+                fold_ds_rn(tot[c], lo[c], part);
+            else
+                tot[c] = __fadd_rn(tot[c], part);
+        }
+    }
+}
+
 // Sums of the acceleration and jerk terms of Eq. (Force) for rows 0 .. cnt-1
 // over the first L entries (a multiple of 4) of a copy of j-particles in shared
 // memory, entry e holding particle j0 + e.  Layout: structure of arrays of
-// `stride` floats each (x, y, z, m, vx, vy, vz, and the lo parts of x, y, z in
+// `stride` floats each (STRIDE when it is positive, else stride_rt; x, y, z, m,
+// vx, vy, vz, and the lo parts of x, y, z in
 // compensated mode), or in the double-single mode four float4 arrays (x, m),
 // (x_lo, m_lo), v, v_lo.  T threads per row (a power of two; NT / T rows per
 // pass): thread `sub` of a row takes the groups of 4 entries 4 (g T + sub),
@@ -27,15 +72,15 @@ namespace nb {
 // double-single mode load_ds(r, live, xi, vi) does the same with double-single
 // i-data.  store(r, tot, lo) takes the row's six sums (one thread per row).
 // Every thread of the block calls this function: it holds block barriers.
-template <int MODE, int NT, class LoadI, class LoadDS, class Store>
-__device__ __forceinline__ void rows_force(const float *jsm, const int stride, const int j0, const int L,
+template <int MODE, int NT, int STRIDE = 0, class LoadI, class LoadDS, class Store>
+__device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt, const int j0, const int L,
                                            const int cnt, const int T, const float eps2, const float eps2_lo,
                                            LoadI &&load_i, LoadDS &&load_ds, Store &&store,
                                            float (*wred)[6][2])
 {
     constexpr bool DSM = MODE == kModeDS;
     constexpr bool DSW = MODE == kModeComp || DSM;  // two-word sums
-    constexpr int NA = SoaTile<MODE == kModeDS ? kModePlain : MODE>::NA;
+    const int stride = STRIDE > 0 ? STRIDE : stride_rt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rpp = NT / T;
     const int TW = T < 32 ? T : 32;
@@ -73,38 +118,13 @@ __device__ __forceinline__ void rows_force(const float *jsm, const int stride, c
             I2 I;
             const int gi = load_i(rr, live, I);
             const int my = warp_live ? (L / 4 - sub + T - 1) / T : 0;  // this thread's groups of 4 j
-            for (int g0 = 0; g0 < my; g0 += 32) {  // folds of 128 terms
-                const int ge = min(g0 + 32, my);
-                f2_t p[7];
-#pragma unroll
-                for (int c = 0; c < 7; ++c) p[c] = 0ull;
-#pragma unroll 2
-                for (int g = g0; g < ge; ++g) {
-                    const int jj = (g * T + sub) * 4;
-                    f2_t v[NA][2];
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) {
-                        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * stride + jj]);
-                        v[a][0] = q.x;
-                        v[a][1] = q.y;
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        pair_term_x2<MODE, true>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
-                                                 DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
-                                                 DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, j0 + jj + 2 * h, gi, p);
-                }
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
-                    float e, o;
-                    f2_unpack(p[c], e, o);
-                    const float part = e + o;
-                    if (DSW)
-                        fold_ds_rn(tot[c], lo[c], part);
-                    else
-                        tot[c] = __fadd_rn(tot[c], part);
-                }
-            }
+            // with eps > 0 the pair j = i adds exact zeros to the acceleration and jerk (dx = dv = 0,
+            // r^2 = eps^2, m r^-3 finite for eps^2 >= 1e-12 and m < 1e20), so only a tiny or zero eps
+            // needs the mask; the choice is the same for every thread
+            if (eps2 >= 1e-12f)
+                rows_sums_x2<MODE, false, STRIDE>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
+            else
+                rows_sums_x2<MODE, true, STRIDE>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
         }
         // the T sums of a row: a butterfly within the warp, then warp by warp
         for (int o = 1; o < (warp_live ? TW : 1); o <<= 1) {

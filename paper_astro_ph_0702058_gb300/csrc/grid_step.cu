@@ -75,20 +75,23 @@ struct GrArgs {
 };
 
 // Dynamic shared memory of a CTA: the prediction of its particles (NA arrays of
-// chunk floats), their due ticks and its rows of a block.
-template <int MODE>
-constexpr size_t gr_smem(const int chunk)
+// SJ >= chunk floats: a compile-time stride folds into the force loop's load
+// offsets; the kernel is built for a few strides, the smallest that holds the
+// chunk is launched), their due ticks and its rows of a block.
+constexpr int kGrStrides[4] = {512, 1024, 2048, kGrMaxChunk};
+template <int MODE, int SJ>
+constexpr size_t gr_smem()
 {
-    return static_cast<size_t>(chunk) * (SoaTile<MODE>::NA * sizeof(float) + sizeof(unsigned long long) + sizeof(int));
+    return static_cast<size_t>(SJ) * (SoaTile<MODE>::NA * sizeof(float) + sizeof(unsigned long long) + sizeof(int));
 }
 
-template <int MODE>
+template <int MODE, int SJ>
 __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A)
 {
     constexpr int NA = SoaTile<MODE>::NA;
     constexpr bool DSW = MODE == kModeComp;
     constexpr int PW = DSW ? 12 : 6;  // floats per partial
-    extern __shared__ __align__(16) float jsm[];  // NA x chunk: x, y, z, m, vx, vy, vz (, x_lo, y_lo, z_lo)
+    extern __shared__ __align__(16) float jsm[];  // NA x SJ: x, y, z, m, vx, vy, vz (, x_lo, y_lo, z_lo)
     __shared__ float f_hi[kGrThreads][6], f_lo[kGrThreads][6];  // forces of up to kGrThreads own rows
     __shared__ float wred[kGrWarps][6][2];
     __shared__ unsigned long long red_u64[32];
@@ -98,8 +101,8 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
     __shared__ unsigned s_flags;
 
     const int CH = A.chunk;
-    unsigned long long *due_c = reinterpret_cast<unsigned long long *>(jsm + NA * CH);  // CH (16-byte aligned)
-    int *own = reinterpret_cast<int *>(due_c + CH);  // this CTA's rows of the block (particle indices, ascending)
+    unsigned long long *due_c = reinterpret_cast<unsigned long long *>(jsm + NA * SJ);  // CH used (16-byte aligned)
+    int *own = reinterpret_cast<int *>(due_c + SJ);  // this CTA's rows of the block (particle indices, ascending)
     const int G = static_cast<int>(gridDim.x), g = static_cast<int>(blockIdx.x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const State &S = A.S;
@@ -115,8 +118,8 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
                                                         (int64_t(1) << (A.lmax - ld_state<true>(S.level + lo + k))))
                       : ~0ull;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) jsm[a * CH + k] = in ? 0.0f : (a < 3 ? kPadPosition : 0.0f);
-        if (in) jsm[3 * CH + k] = A.mass_j[lo + k];
+        for (int a = 0; a < NA; ++a) jsm[a * SJ + k] = in ? 0.0f : (a < 3 ? kPadPosition : 0.0f);
+        if (in) jsm[3 * SJ + k] = A.mass_j[lo + k];
     }
     __syncthreads();
 
@@ -214,9 +217,9 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
                     predict_dim(ld_state<true>(S.x[c] + i), ld_state<true>(S.v[c] + i), ld_state<true>(S.a[c] + i),
                                 ld_state<true>(S.k[c] + i), pd, xp, vp);
                     const float h = d2f_rn(xp);
-                    jsm[c * CH + k] = h;
-                    jsm[(4 + c) * CH + k] = d2f_rn(vp);
-                    if (DSW) jsm[(7 + c) * CH + k] = d2f_rn(xp - f2d(h));  // the difference is exact
+                    jsm[c * SJ + k] = h;
+                    jsm[(4 + c) * SJ + k] = d2f_rn(vp);
+                    if (DSW) jsm[(7 + c) * SJ + k] = d2f_rn(xp - f2d(h));  // the difference is exact
                 }
             }
         }
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
 #pragma unroll
             for (int a = 0; a < NA; ++a)
                 if (a != 3 && NB_CHECK(off + q < RM, A.st, 9))
-                    A.ri[(a < 3 ? a : a - 1) * RM + off + q] = jsm[a * CH + k];
+                    A.ri[(a < 3 ? a : a - 1) * RM + off + q] = jsm[a * SJ + k];
         }
         if (!barrier()) break;
 
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
                     if (DSW) d[6 + c] = lw[c];
                 }
             };
-            rows_force<MODE, kGrThreads>(jsm, CH, lo, L, na, T, A.eps2, 0.0f, load_i, no_ds, store, wred);
+            rows_force<MODE, kGrThreads, SJ>(jsm, SJ, lo, L, na, T, A.eps2, 0.0f, load_i, no_ds, store, wred);
         }
         if (!barrier()) break;
 
@@ -323,11 +326,6 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
     }
 }
 
-template <int MODE>
-size_t gr_smem_max()
-{
-    return gr_smem<MODE>(kGrMaxChunk);
-}
 
 // CTAs of the mode's launch on this device (one per SM), or 0 when it cannot
 // launch cooperatively with the largest shared memory; found once per mode.
@@ -342,8 +340,8 @@ int grid_size_for()
             cudaGetLastError();
             return 0;
         }
-        auto kern = grid_step_kernel<MODE>;
-        const size_t smem = gr_smem_max<MODE>();
+        auto kern = grid_step_kernel<MODE, kGrMaxChunk>;
+        const size_t smem = gr_smem<MODE, kGrMaxChunk>();
         int per_sm = 0;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
                 cudaSuccess ||
@@ -355,6 +353,26 @@ int grid_size_for()
         return sms;
     }();
     return size;
+}
+
+// Launches the instance of stride SJ (its shared-memory limit raised once).
+template <int MODE, int SJ>
+cudaError_t launch_sj(cudaLaunchConfig_t cfg, const GrArgs &A)
+{
+    static const cudaError_t set = cudaFuncSetAttribute(grid_step_kernel<MODE, SJ>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        static_cast<int>(gr_smem<MODE, SJ>()));
+    if (set != cudaSuccess) return set;
+    cfg.dynamicSmemBytes = gr_smem<MODE, SJ>();
+    return cudaLaunchKernelEx(&cfg, grid_step_kernel<MODE, SJ>, A);
+}
+template <int MODE>
+cudaError_t launch_mode(const cudaLaunchConfig_t &cfg, const GrArgs &A)
+{
+    if (A.chunk <= kGrStrides[0]) return launch_sj<MODE, kGrStrides[0]>(cfg, A);
+    if (A.chunk <= kGrStrides[1]) return launch_sj<MODE, kGrStrides[1]>(cfg, A);
+    if (A.chunk <= kGrStrides[2]) return launch_sj<MODE, kGrStrides[2]>(cfg, A);
+    return launch_sj<MODE, kGrStrides[3]>(cfg, A);
 }
 
 // The scratch: barrier counter, published records, row buffer, partials, each
@@ -434,15 +452,13 @@ cudaError_t grid_step_launch(int mode, const State &S, const JStream &J, double 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kGrThreads);
-    cfg.dynamicSmemBytes = mode == kModeComp ? gr_smem<kModeComp>(CH) : gr_smem<kModePlain>(CH);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = mode == kModeComp ? cudaLaunchKernelEx(&cfg, grid_step_kernel<kModeComp>, A)
-                          : cudaLaunchKernelEx(&cfg, grid_step_kernel<kModePlain>, A);
+    e = mode == kModeComp ? launch_mode<kModeComp>(cfg, A) : launch_mode<kModePlain>(cfg, A);
     if (e == cudaSuccess) ++*launches;
     return e;
 }
