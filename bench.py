@@ -609,7 +609,8 @@ def block_run(args):
         pairs = st["pairs"] - p0
         rows.append({"mode": mode, "blocks": int(blocks), "mean_block": pairs / max(1, blocks) / (n - 1),
                      "pairs": int(pairs), "wall_s": wall, "pairs_per_s": pairs / wall, "init_s": t_init,
-                     "energy_error": abs((e1 - e0) / e0), "below_dt_min": int(st["below_dt_min"])})
+                     "energy_error": abs((e1 - e0) / e0), "below_dt_min": int(st["below_dt_min"]),
+                     "grid_blocks": int(st["grid_blocks"])})
     print(json.dumps({"workload": args.workload, "n": n, "eps2": eps2, "eta": 0.02, "t_end": t_end,
                       "rows": rows}), flush=True)
 
@@ -651,7 +652,8 @@ def table2_run(args):
             pairs = st["pairs"] - st0["pairs"]
             rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "pairs": int(pairs),
                          "pairs_per_s": pairs / wall, "energy_error": abs((e1 - e0) / e0),
-                         "cluster_blocks": int(st["cluster_blocks"] - st0["cluster_blocks"])})
+                         "cluster_blocks": int(st["cluster_blocks"] - st0["cluster_blocks"]),
+                         "grid_blocks": int(st["grid_blocks"] - st0["grid_blocks"])})
         out.append({"n": n, "rows": rows, "paper_wall_s": TABLE2_PAPER_S.get(n)})
     print(json.dumps({"workload": "table2", "eps2": eps2, "eta": eta, "dt_max": 0.125, "timed": [0.25, 0.5],
                       "runs": out, "context": "paper Table 2: other hardware, FP32 on the GPUs; not a target"}),

@@ -279,14 +279,24 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
                 float h[6], l[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) h[c] = l[c] = 0.0f;
-                for (int r = lane; r < G; r += 32)
+                for (int r0 = 0; r0 < G; r0 += 96) {  // lane takes CTAs lane, lane + 32, ...: three loaded at once
+                    float x[3][PW];
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        if (DSW)
-                            ds2_add(h[c], l[c], __ldcg(src + r * PW + c), __ldcg(src + r * PW + 6 + c));
-                        else
-                            h[c] = __fadd_rn(h[c], __ldcg(src + r * PW + c));
+                    for (int u = 0; u < 3; ++u) {
+                        const int r = r0 + 32 * u + lane;
+#pragma unroll
+                        for (int c = 0; c < PW; ++c) x[u][c] = r < G ? __ldcg(src + r * PW + c) : 0.0f;
                     }
+#pragma unroll
+                    for (int u = 0; u < 3; ++u)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {
+                            if (DSW)
+                                ds2_add(h[c], l[c], x[u][c], x[u][6 + c]);
+                            else
+                                h[c] = __fadd_rn(h[c], x[u][c]);
+                        }
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
