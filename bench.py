@@ -549,12 +549,13 @@ def c1_run(args):
             wall = time.perf_counter() - t0
             e1 = sum(sim.energy())
             st = sim.stats()
-        # cluster_blocks: blocks run by the one-cluster kernel; graph_blocks: blocks run inside
+        # cluster_blocks / grid_blocks: blocks run by the one-cluster / whole-GPU kernel; graph_blocks: blocks run inside
         # step-graph replays; loop_blocks: of those, the ones the device-side loop ran without a host
         # round trip
         rows.append({"mode": mode, "blocks": int(blocks), "wall_s": wall, "us_per_block": wall / max(blocks, 1) * 1e6,
                      "energy_error": abs((e1 - e0) / e0), "cluster_blocks": int(st["cluster_blocks"]),
-                     "graph_blocks": int(st["graph_blocks"]), "loop_blocks": int(st["loop_blocks"])})
+                     "grid_blocks": int(st["grid_blocks"]), "graph_blocks": int(st["graph_blocks"]),
+                     "loop_blocks": int(st["loop_blocks"])})
     nbody_debug_step_graphs(3)
     if args.no_cpu_baseline:
         print(json.dumps({"workload": "c1", "n": n, "eps2": eps2, "eta": 0.01, "t_end": t_end, "rows": rows}),

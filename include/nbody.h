@@ -258,8 +258,11 @@ void nbody_debug_fail_alloc(int k);
 /* Test hook: while on (nonzero), force kernels launched from this process do
  * not issue the copy of their first j-tile, so each block's bounded wait for
  * that tile gives up after about 2 s; the kernel records the timeout and
- * returns, and the call reports NBODY_ETIMEOUT.  Nothing faults or hangs and
- * the context stays usable.  Exercises the failure path of the device waits. */
+ * returns, and the call reports NBODY_ETIMEOUT.  Likewise the last CTA of the
+ * whole-GPU block-step kernel (level 3 of nbody_debug_step_graphs) leaves
+ * before its first grid barrier, whose bounded wait in the other CTAs gives up
+ * after about 1 s.  Nothing faults or hangs and the context stays usable.
+ * Exercises the failure path of the device waits. */
 void nbody_debug_skip_tile_copy(int on);
 
 /* Test switch for how nbody_step runs blocks small enough for one captured

@@ -184,7 +184,8 @@ int absorb_status(nbody_ctx *c)
     if (f & kFlagDebugBounds)
         return fail(NBODY_ECUDA, "debug build: a device-side index check failed at site %d (access skipped)",
                     h.debug_site);
-    if (f & kFlagTimeout) return fail(NBODY_ETIMEOUT, "a device-side wait for a j-tile gave up (bounded wait)");
+    if (f & kFlagTimeout)
+        return fail(NBODY_ETIMEOUT, "a bounded device-side wait (for a j-tile or at a grid barrier) gave up");
     if (f & kFlagBadIndex)
         return fail(NBODY_EINVAL, "active list row %d holds an index outside [0, %lld)", h.bad_index,
                     static_cast<long long>(c->n));

@@ -64,6 +64,7 @@ struct GrArgs {
     int lmin, lmax;
     long long t_end, budget, last_t;
     unsigned stop_flags;
+    int skip_arrival;  // test hook: the last CTA leaves before its first barrier (the others' wait gives up)
     DevStatus *st;
     SchedOut *sched_out;
     StepLoop *L;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
             A.pub[g].cnt = cnt;
             A.pub[g].flags = __ldcg(&A.st->flags);
         }
+        if (A.skip_arrival && done == 0 && g == G - 1) break;
         if (!barrier()) break;
 
         // 2. the block time and size, where this CTA's rows start, the decision (all alike)
@@ -446,6 +448,7 @@ cudaError_t grid_step_launch(int mode, const State &S, const JStream &J, double 
     A.budget = budget;
     A.last_t = last_t;
     A.stop_flags = stop_flags;
+    A.skip_arrival = g_skip_first_copy;
     A.st = st;
     A.sched_out = sched_out;
     A.L = L;

@@ -4,8 +4,9 @@ A failed check records an error word and skips the access; the host reports it a
 NBODY_ECUDA ("debug build: a device-side index check failed at site ...").  Nothing traps.
 This builds the library with the checks into a temporary directory and runs, in a fresh
 process loading that build, force evaluations over launch shapes, modes and block sizes,
-block runs through the device-side loop and through separate launches, the ensemble and
-the no-alloc entry point; every call must succeed (no check may fail)."""
+block runs through the device-side loop, the one-cluster and the whole-GPU block-step kernels
+and separate launches, the ensemble and the no-alloc entry point; every call must succeed (no
+check may fail)."""
 import os
 import subprocess
 import sys
@@ -44,9 +45,12 @@ for level in (3, 2, 0):
             sim.step(1.0 / 64)
             sim.energy(); sim.energy(ds_potential=True)
 nbody_debug_step_graphs(3)
-m, x, v = plummer_sphere(20000, 2)
-with Simulation(m, x, v, EPS2, eta=0.02, mode="comp") as sim:
-    sim.step(1.0 / 64)
+for n in (4099, 20000):  # the whole-GPU block-step kernel (4099: CTAs without particles)
+    m, x, v = plummer_sphere(n, 2)
+    for mode in ("plain", "comp"):
+        with Simulation(m, x, v, EPS2, eta=0.02, mode=mode) as sim:
+            sim.step(1.0 / 64)
+            assert sim.stats()["grid_blocks"] > 0
 sizes = ensemble_sizes(8, 4)
 parts = [plummer_sphere(int(k), 40 + c) for c, k in enumerate(sizes)]
 with Ensemble(sizes, *(np.concatenate([p[i] for p in parts]) for i in range(3)), EPS2, eta=0.02) as ens:

@@ -160,3 +160,32 @@ def test_grid_kernel_not_taken_outside_its_scope(torch, n, mode, kw):
         nb = sim.step(1.0 / 64, 3)
         st = sim.stats()
     assert nb > 0 and st["grid_blocks"] == 0
+
+
+def test_grid_barrier_times_out_and_context_survives(torch):
+    """The test hook makes the grid kernel's last CTA leave before its first barrier, so the other CTAs'
+    bounded wait gives up after ~1 s: the call reports NBODY_ETIMEOUT without a fault or a hang, no block
+    has run, and the next call continues as if the failed one had not happened."""
+    import time
+    from paper_astro_ph_0702058_gb300 import NBodyError, nbody_debug_skip_tile_copy
+    m, x, v = plummer_sphere(8192, 4)
+    with _sim(m, x, v, "comp") as ref:
+        nb_ref = ref.step(1.0 / 64)
+        s_ref = _state(ref)
+    with _sim(m, x, v, "comp") as sim:
+        nbody_debug_skip_tile_copy(True)
+        try:
+            t0 = time.perf_counter()
+            with pytest.raises(NBodyError) as e:
+                sim.step(1.0 / 64)
+            waited = time.perf_counter() - t0
+        finally:
+            nbody_debug_skip_tile_copy(False)
+        assert e.value.code == -7, e.value
+        assert 0.5 < waited < 30.0
+        assert sim.stats()["blocks"] == 0
+        nb = sim.step(1.0 / 64)
+        s = _state(sim)
+        assert nb == nb_ref and sim.stats()["grid_blocks"] > 0
+    for key in s:
+        assert np.array_equal(s[key], s_ref[key]), key
