@@ -80,6 +80,35 @@ def test_grid_blocks_against_the_oracle(torch, mode, n, blocks):
     assert ran > 0, "no block ran in the grid kernel"
 
 
+@pytest.mark.parametrize("mode,eps2", [("plain", 0.0), ("comp", 0.0), ("comp", 1e-14)])
+def test_grid_blocks_unsoftened_against_the_oracle(torch, mode, eps2):
+    """eps = 0 (and eps^2 below 1e-12): the grid kernel masks the pair j = i (with a softening it adds exact
+    zeros and is not masked).  One block per call against the FP64 oracle: list, forces within the per-row
+    FP32 bound, corrected state and levels."""
+    from paper_astro_ph_0702058_gb300 import Simulation
+    n, eta = 6000, 0.02
+    m, x, v = plummer_sphere(n, 9)
+    with Simulation(m, x, v, eps2, eta=eta, lmin=LMIN, lmax=LMAX, mode=mode) as sim:
+        g = _state(sim)
+        for b in range(6):
+            tick, act = oracle.schedule(g["t_tick"], g["level"], LMAX)
+            before = sim.stats()["grid_blocks"]
+            assert sim.step(1.0, 1) == 1
+            assert sim.stats()["grid_blocks"] == before + (1 if len(act) <= GRID_ROWS else 0), b
+            g2 = _state(sim)
+            st = oracle.State(m, g["x"], g["v"], eps2, eta, lmin=LMIN, lmax=LMAX)
+            st.a[:], st.k[:], st.t[:], st.level[:] = g["a"], g["k"], g["t_tick"], g["level"]
+            xp, vp = st.predict(tick)
+            ra, rk, rp = oracle.force(m, xp, vp, eps2, act)
+            acc, jerk = g2["a"][act], g2["k"][act]
+            assert np.all(np.isfinite(acc)) and np.all(np.isfinite(jerk)), b
+            check_force(mode, m, xp, vp, eps2, act, (acc, jerk, rp), (ra, rk, rp), f"eps2={eps2} block {b}")
+            st.correct(act, xp, vp, acc, jerk, tick)
+            assert np.array_equal(g2["level"], st.level) and np.array_equal(g2["t_tick"], st.t), b
+            g = g2
+        assert sim.stats()["grid_blocks"] > 0
+
+
 @pytest.mark.parametrize("mode", ["plain", "comp"])
 def test_grid_run_is_independent_of_launch_budget(torch, mode):
     """One launch per run of small blocks, or launches of at most 5 blocks: the same bits (the
