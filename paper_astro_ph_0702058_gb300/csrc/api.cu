@@ -943,6 +943,7 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
     bool cluster_declined = false;  // the cluster kernel ran none of the blocks it was offered
     const bool grid = !cluster && grid_steps(c);
     bool grid_declined = false;  // likewise the whole-GPU kernel
+    bool grid_pending = false;   // the next block is not scheduled on the host: the grid kernel schedules it
     if (grid && !c->grid_buf) {
         c->grid_rows = static_cast<int>(std::min<int64_t>(kGridRows, c->n));
         NB_CUDA(dev_alloc(&c->grid_buf, grid_step_bytes(c->p.mode, c->grid_rows, grid_step_size(c->p.mode))),
@@ -981,7 +982,8 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
             cluster_declined = blocks == 0;  // that block takes the path below once
             continue;
         }
-        if (grid && !grid_declined && na <= c->grid_rows) {
+        if (grid && !grid_declined && (grid_pending || na <= c->grid_rows)) {
+            grid_pending = false;
             StepLoop *L = c->loop_host;
             const int64_t left = max_steps > 0 ? max_steps - done : kClusterCap;
             NB_CUDA(grid_step_launch(c->p.mode, c->S, c->J, c->eps2, c->p.eta, c->p.lmin, c->p.lmax, tend,
@@ -1004,6 +1006,11 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
                 c->t_max = std::max(c->t_max, static_cast<int64_t>(L->last_t));
                 c->t_pred = L->last_t;
                 c->pred_valid = false;
+                c->force_n_act = -1;
+            }
+            if (L->predicted >= 0) {  // it stopped at a larger block and left the j-stream predicted to its time
+                c->t_pred = L->predicted;
+                c->pred_valid = true;
                 c->force_n_act = -1;
             }
             done += blocks;
@@ -1062,8 +1069,10 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
             na = c->sched_host->n_act;
             continue;
         }
-        r = predict_internal(c, tb);
-        if (r != NBODY_OK) break;
+        if (!(grid && c->pred_valid && c->t_pred == tb)) {
+            r = predict_internal(c, tb);
+            if (r != NBODY_OK) break;
+        }
         NB_CUDA(cudaMemcpyAsync(c->act_force, c->act_sched, static_cast<size_t>(na) * sizeof(int32_t),
                                 cudaMemcpyDeviceToDevice, c->s),
                 "list copy");
@@ -1072,6 +1081,10 @@ int nbody_step(nbody_ctx *c, double t_end, int64_t max_steps, int64_t *n_steps)
         r = correct_internal(c, c->act_sched, na, c->f_acc, c->f_jerk, true);
         if (r != NBODY_OK) break;
         ++done;
+        if (grid) {  // the grid kernel schedules the next block (and runs it, when it is small)
+            grid_pending = true;
+            continue;
+        }
         r = schedule_internal(c, &tb, &na);
     }
     if (n_steps) *n_steps = done;

@@ -56,6 +56,8 @@ struct GrPub {
 
 struct GrArgs {
     State S;
+    float *soa;           // the j-stream (kSoaArrays x n_pad floats, structure of arrays)
+    int64_t n_pad;
     const float *mass_j;  // the j-stream's masses (float), n entries
     int chunk;            // particles per CTA, a multiple of 4
     int rows_max;         // largest block this launch runs; rows of the row buffer
@@ -130,7 +132,25 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
         if (tid == 0) atomicOr(&A.st->flags, static_cast<unsigned>(kFlagTimeout));
         return false;
     };
-    long long done = 0, rows = 0, last_t = A.last_t;
+    // this CTA's particles predicted to tick t: array a of particle lo + k at dst[a * stride + base + k]
+    // (x, y, z, vx, vy, vz and, compensated, the lo parts of x, y, z: the predictor kernel's values)
+    auto predict_own = [&](const unsigned long long t, float *dst, const int64_t stride, const int64_t base) {
+        for (int k = tid; k < nown; k += kGrThreads) {
+            const int i = lo + k;
+            const PredDt pd = pred_dt(static_cast<double>(static_cast<int64_t>(t) - ld_state<true>(S.t + i)) * A.tick);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double xp, vp;
+                predict_dim(ld_state<true>(S.x[c] + i), ld_state<true>(S.v[c] + i), ld_state<true>(S.a[c] + i),
+                            ld_state<true>(S.k[c] + i), pd, xp, vp);
+                const float h = d2f_rn(xp);
+                dst[c * stride + base + k] = h;
+                dst[(4 + c) * stride + base + k] = d2f_rn(vp);
+                if (DSW) dst[(7 + c) * stride + base + k] = d2f_rn(xp - f2d(h));  // the difference is exact
+            }
+        }
+    };
+    long long done = 0, rows = 0, last_t = A.last_t, predicted = -1;
     unsigned long long tb = ~0ull;
     int na = 0;
     for (;;) {
@@ -207,24 +227,15 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
                         na > 0 && na <= RM;
         for (int q = tid; q < mine; q += kGrThreads)
             if (NB_CHECK(off + q < n, A.st, 8)) A.act_out[off + q] = own[q];
-        if (!go) break;
-        {  // this CTA's particles predicted to tb, into shared memory
-            for (int k = tid; k < nown; k += kGrThreads) {
-                const int i = lo + k;
-                const PredDt pd =
-                    pred_dt(static_cast<double>(static_cast<int64_t>(tb) - ld_state<true>(S.t + i)) * A.tick);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    double xp, vp;
-                    predict_dim(ld_state<true>(S.x[c] + i), ld_state<true>(S.v[c] + i), ld_state<true>(S.a[c] + i),
-                                ld_state<true>(S.k[c] + i), pd, xp, vp);
-                    const float h = d2f_rn(xp);
-                    jsm[c * SJ + k] = h;
-                    jsm[(4 + c) * SJ + k] = d2f_rn(vp);
-                    if (DSW) jsm[(7 + c) * SJ + k] = d2f_rn(xp - f2d(h));  // the difference is exact
-                }
+        if (!go) {
+            if (done < A.budget && (s_flags & A.stop_flags) == 0u && static_cast<long long>(tb) <= A.t_end &&
+                na > RM) {  // the separate kernels run this block: leave them the prediction
+                predict_own(tb, A.soa, A.n_pad, lo);
+                predicted = static_cast<long long>(tb);
             }
+            break;
         }
+        predict_own(tb, jsm, SJ, 0);  // this CTA's particles predicted to tb, into shared memory
         __syncthreads();
         for (int q = tid; q < mine; q += kGrThreads) {  // the rows' predicted data for every CTA
             const int k = own[q] - lo;
@@ -335,6 +346,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
         A.L->blocks = done;
         A.L->rows = rows;
         A.L->last_t = last_t;
+        A.L->predicted = predicted;
     }
 }
 
@@ -436,6 +448,8 @@ cudaError_t grid_step_launch(int mode, const State &S, const JStream &J, double 
     if (G == 0 || CH == 0 || rows_max < 1 || !J.soa || !buf) return cudaErrorInvalidValue;
     GrArgs A;
     A.S = S;
+    A.soa = J.soa;
+    A.n_pad = J.n_pad;
     A.mass_j = J.soa + 3 * J.n_pad;
     A.chunk = CH;
     A.rows_max = rows_max;

@@ -192,6 +192,7 @@ struct StepLoop {
     long long blocks;  // blocks it added
     long long rows;    // their active rows
     long long last_t;  // block time of the last block that ran
+    long long predicted;  // whole-GPU block-step kernel: the tick it left the j-stream predicted to, or -1
 };
 // What the loop's decision reads: the next block (scheduled in the same body)
 // runs when no flag of stop_flags is raised in st, it is due by L->t_end, its
@@ -231,7 +232,11 @@ cudaError_t cluster_step_launch(int mode, const State &S, const JStream &J, doub
 // Block steps of larger systems (n <= CTAs x kGrMaxChunk) as one cooperative
 // launch of one CTA per SM, packed plain and compensated modes, with the same
 // contract as cluster_step_launch; `buf` is grid_step_bytes(mode, rows_max,
-// grid_step_size(mode)) bytes of device scratch.
+// grid_step_size(mode)) bytes of device scratch.  When it stops at a block
+// larger than rows_max (with budget left, due by t_end, no stop flag) it also
+// leaves the j-stream (J.soa) predicted to that block's time and sets
+// L->predicted to it (else -1), so the separate kernels can run the block
+// without the predictor.
 constexpr int kGrMaxChunk = 3584;  // particles per CTA (their prediction is held in shared memory)
 // CTAs of the mode's launch on this device (one per SM), or 0 (no cooperative launch).
 int grid_step_size(int mode);
