@@ -745,7 +745,7 @@ int64_t graph_rows_for(const nbody_ctx *c)
 bool same_shape(const ForceConfig &a, const ForceConfig &b)
 {
     return a.threads == b.threads && a.ipt == b.ipt && a.jsub == b.jsub && a.split == b.split &&
-           a.tiles_per_split == b.tiles_per_split;
+           a.tiles_per_split == b.tiles_per_split && a.slice == b.slice;
 }
 
 // One block step sized for graph_rows rows, captured on cs: predictor, force,

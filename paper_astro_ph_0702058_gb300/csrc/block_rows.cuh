@@ -10,39 +10,65 @@
 
 namespace nb {
 
-// One thread's part of a row in rows_force: the groups of 4 j (g T + sub) 4,
-// g < my, of the shared-memory copy, folded every 128 terms into (tot, lo).
-template <int MODE, bool SELF, int STRIDE>
-__device__ __forceinline__ void rows_sums_x2(const float *jsm, const int stride_rt, const int j0, const int my,
-                                             const int T, const int sub, const I2 &I, const int gi, const f2_t E2,
-                                             const f2_t NEG3, float (&tot)[6], float (&lo)[6])
+// Pair terms of NG groups of 4 j (g T + sub) 4, g = g0 .. g0 + NG - 1 (NG = 0:
+// ng of them), of the shared-memory copy, into the packed partials p.  ONE:
+// T = 1 (consecutive groups).  A fixed NG gives the loop a compile-time trip
+// count.
+template <int MODE, bool SELF, int STRIDE, bool ONE, int NG>
+__device__ __forceinline__ void rows_groups_x2(const float *jsm, const int stride, const int j0, const int g0,
+                                               const int ng, const int T, const int sub, const I2 &I, const int gi,
+                                               const f2_t E2, const f2_t NEG3, f2_t (&p)[7])
 {
     constexpr bool DSW = MODE == kModeComp;
     constexpr int NA = SoaTile<MODE>::NA;
-    const int stride = STRIDE > 0 ? STRIDE : stride_rt;  // a compile-time stride folds into the load offsets
+    const int n_it = NG > 0 ? NG : ng;
+#pragma unroll 2
+    for (int u = 0; u < n_it; ++u) {
+        const int g = g0 + u;
+        const int jj = ONE ? 4 * g : (g * T + sub) * 4;
+        f2_t v[NA][2];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * (STRIDE > 0 ? STRIDE : stride) + jj]);
+            v[a][0] = q.x;
+            v[a][1] = q.y;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
+                                     DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull, DSW ? v[NA - 1][h] : 0ull,
+                                     I, E2, NEG3, j0 + jj + 2 * h, gi, p);
+    }
+}
+
+// One thread's part of a row in rows_force: the groups of 4 j (g T + sub) 4,
+// g < my, of the shared-memory copy, folded every 128 terms (32 groups) into
+// (tot, lo): acceleration and jerk, and with POT the potential.
+template <int MODE, bool SELF, int STRIDE, bool POT>
+__device__ __forceinline__ void rows_sums_x2(const float *jsm, const int stride_rt, const int j0, const int my,
+                                             const int T, const int sub, const I2 &I, const int gi, const f2_t E2,
+                                             const f2_t NEG3, float (&tot)[7], float (&lo)[7])
+{
+    constexpr bool DSW = MODE == kModeComp;
+    constexpr int NS = POT ? 7 : 6;
+    const int stride = STRIDE > 0 ? STRIDE : stride_rt;
     for (int g0 = 0; g0 < my; g0 += 32) {  // folds of 128 terms
-        const int ge = min(g0 + 32, my);
         f2_t p[7];
 #pragma unroll
         for (int c = 0; c < 7; ++c) p[c] = 0ull;
-#pragma unroll 2
-        for (int g = g0; g < ge; ++g) {
-            const int jj = (g * T + sub) * 4;
-            f2_t v[NA][2];
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&jsm[a * stride + jj]);
-                v[a][0] = q.x;
-                v[a][1] = q.y;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                pair_term_x2<MODE, SELF>(v[0][h], v[1][h], v[2][h], v[3][h], v[4][h], v[5][h], v[6][h],
-                                         DSW ? v[NA - 3][h] : 0ull, DSW ? v[NA - 2][h] : 0ull,
-                                         DSW ? v[NA - 1][h] : 0ull, I, E2, NEG3, j0 + jj + 2 * h, gi, p);
+        // a full fold with a compile-time trip count: 2-3 % faster in plain mode; the compensated mode's
+        // 128-register kernels measured slower with it (the C2 free run 1.74 -> 1.78 s)
+        if (MODE == kModePlain && g0 + 32 <= my) {
+            if (T == 1)
+                rows_groups_x2<MODE, SELF, STRIDE, true, 32>(jsm, stride, j0, g0, 32, T, sub, I, gi, E2, NEG3, p);
+            else
+                rows_groups_x2<MODE, SELF, STRIDE, false, 32>(jsm, stride, j0, g0, 32, T, sub, I, gi, E2, NEG3, p);
+        } else {
+            rows_groups_x2<MODE, SELF, STRIDE, false, 0>(jsm, stride, j0, g0, min(32, my - g0), T, sub, I, gi, E2,
+                                                         NEG3, p);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {  // acc and jerk (the corrector needs no potential)
+        for (int c = 0; c < NS; ++c) {
             float e, o;
             f2_unpack(p[c], e, o);
             const float part = e + o;
@@ -70,14 +96,19 @@ __device__ __forceinline__ void rows_sums_x2(const float *jsm, const int stride_
 // by warp through wred.  load_i(r, live, I) fills the packed i-data of row r
 // (row 0's when !live) and returns its particle index (-1 when !live); in the
 // double-single mode load_ds(r, live, xi, vi) does the same with double-single
-// i-data.  store(r, tot, lo) takes the row's six sums (one thread per row).
-// Every thread of the block calls this function: it holds block barriers.
-template <int MODE, int NT, int STRIDE = 0, class LoadI, class LoadDS, class Store>
+// i-data.  store(r, tot, lo) takes the row's sums (one thread per row): six,
+// and with POT (packed modes) the potential as the seventh.  The pair j = i is
+// masked in the warps holding a row whose particle lies in the entries, where
+// it matters: for the potential, or for a softening too small to keep its
+// zero terms finite.  Every thread of the block calls this function: it holds
+// block barriers.
+template <int MODE, int NT, int STRIDE = 0, bool POT = false, class LoadI, class LoadDS, class Store>
 __device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt, const int j0, const int L,
                                            const int cnt, const int T, const float eps2, const float eps2_lo,
                                            LoadI &&load_i, LoadDS &&load_ds, Store &&store,
-                                           float (*wred)[6][2])
+                                           float (*wred)[7][2])
 {
+    constexpr int NS = POT ? 7 : 6;
     constexpr bool DSM = MODE == kModeDS;
     constexpr bool DSW = MODE == kModeComp || DSM;  // two-word sums
     const int stride = STRIDE > 0 ? STRIDE : stride_rt;
@@ -91,9 +122,9 @@ __device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt
         const int sub = tid % T;
         const bool live = rr < cnt;
         const bool warp_live = q0 + warp * 32 / T < cnt;  // a warp with no row skips the sums
-        float tot[6], lo[6];
+        float tot[7], lo[7];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) tot[c] = lo[c] = 0.0f;
+        for (int c = 0; c < 7; ++c) tot[c] = lo[c] = 0.0f;
         if constexpr (DSM) {
             const float4 *sp = reinterpret_cast<const float4 *>(jsm);
             dsa::ds xi[3], vi[3];
@@ -119,17 +150,19 @@ __device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt
             const int gi = load_i(rr, live, I);
             const int my = warp_live ? (L / 4 - sub + T - 1) / T : 0;  // this thread's groups of 4 j
             // with eps > 0 the pair j = i adds exact zeros to the acceleration and jerk (dx = dv = 0,
-            // r^2 = eps^2, m r^-3 finite for eps^2 >= 1e-12 and m < 1e20), so only a tiny or zero eps
-            // needs the mask; the choice is the same for every thread
-            if (eps2 >= 1e-12f)
-                rows_sums_x2<MODE, false, STRIDE>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
+            // r^2 = eps^2, m r^-3 finite for eps^2 >= 1e-12 and m < 1e20), so only the potential or a
+            // tiny or zero eps needs the mask, and only in a warp with a row whose particle is among the
+            // entries; the choice is the same for every lane of a warp
+            const bool own_row = live && static_cast<unsigned>(gi - j0) < static_cast<unsigned>(L);
+            if (__any_sync(0xffffffffu, own_row) && (POT || eps2 < 1e-12f))
+                rows_sums_x2<MODE, true, STRIDE, POT>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
             else
-                rows_sums_x2<MODE, true, STRIDE>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
+                rows_sums_x2<MODE, false, STRIDE, POT>(jsm, stride, j0, my, T, sub, I, gi, E2, NEG3, tot, lo);
         }
         // the T sums of a row: a butterfly within the warp, then warp by warp
         for (int o = 1; o < (warp_live ? TW : 1); o <<= 1) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
+            for (int c = 0; c < NS; ++c) {
                 const float h2 = __shfl_xor_sync(0xffffffffu, tot[c], o);
                 if (DSW) {
                     const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
@@ -142,7 +175,7 @@ __device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt
         if (T > 32) {
             if (lane == 0)
 #pragma unroll
-                for (int c = 0; c < 6; ++c) {
+                for (int c = 0; c < NS; ++c) {
                     wred[warp][c][0] = tot[c];
                     wred[warp][c][1] = lo[c];
                 }
@@ -150,7 +183,7 @@ __device__ __forceinline__ void rows_force(const float *jsm, const int stride_rt
             if (sub == 0)
                 for (int w = warp + 1; w < warp + T / 32; ++w)
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {
+                    for (int c = 0; c < NS; ++c) {
                         if (DSW)
                             ds2_add(tot[c], lo[c], wred[w][c][0], wred[w][c][1]);
                         else

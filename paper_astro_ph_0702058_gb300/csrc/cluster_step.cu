@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_step_kernel(const ClArg
     __shared__ int row_idx[kClMaxChunk];           // this CTA's share of the block's rows
     __shared__ float f_hi[kClMaxChunk][6], f_lo[kClMaxChunk][6];  // their acc and jerk sums
     __shared__ int warp_tot[kClWarps];
-    __shared__ float wred[kClWarps][6][2];
+    __shared__ float wred[kClWarps][7][2];
     __shared__ unsigned long long red_u64[32];
     __shared__ int b_pre[kClMaxC + 1];
     __shared__ int lists[kClMaxPad];  // CTA r's active particles at r chunk .. (stored by CTA r)

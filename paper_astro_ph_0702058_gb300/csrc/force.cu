@@ -3,7 +3,17 @@
 #include <algorithm>
 #include <cmath>
 
+#include "force_slice.cuh"
 #include "force_x2.cuh"
+
+// Block sizes the automatic shape gives the slice shape (packed plain and
+// compensated modes, streams of kJSubMinTiles tiles or more).
+#ifndef NB_SLICE_MIN_ROWS
+#define NB_SLICE_MIN_ROWS 512
+#endif
+#ifndef NB_SLICE_MAX_ROWS
+#define NB_SLICE_MAX_ROWS 8191
+#endif
 
 namespace nb {
 
@@ -68,6 +78,20 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
                  int req_split, ForceConfig *cfg, int req_jsub)
 {
     const int n_tiles = static_cast<int>(n_pad / kJTile);
+    // the slice shape: one CTA per SM over its slice of the stream, for mid-size blocks when the
+    // caller fixes no parameter and the slice fits shared memory
+    if (NB_PACKED && (mode == kModePlain || mode == kModeComp) && req_threads == 0 && req_ipt == 0 &&
+        req_split <= 0 && req_jsub == 0 && n_act >= NB_SLICE_MIN_ROWS && n_act <= NB_SLICE_MAX_ROWS &&
+        n_tiles >= kJSubMinTiles && slice_chunk(n_pad, sm_count) > 0) {
+        cfg->threads = kSliceThreads;
+        cfg->ipt = 1;
+        cfg->jsub = 1;
+        cfg->split = sm_count;
+        cfg->tiles_per_split = 0;
+        cfg->n_iblk = 1;
+        cfg->slice = 1;
+        return NBODY_OK;
+    }
     int threads = req_threads;
     int ipt = req_ipt;
     // j-subgroups: blocks of kJSubMinRows to 8191 rows in the packed plain and compensated
@@ -157,6 +181,7 @@ int force_choose(int mode, int64_t n_act, int64_t n_pad, int sm_count, int req_t
     cfg->threads = threads;
     cfg->ipt = jsub ? 1 : ipt;
     cfg->jsub = jsub ? kJSub : 1;
+    cfg->slice = 0;
     cfg->split = split;
     cfg->tiles_per_split = tps;
     cfg->n_iblk = n_iblk;

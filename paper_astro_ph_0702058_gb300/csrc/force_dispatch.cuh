@@ -5,6 +5,7 @@
 #pragma once
 
 #include "force_impl.cuh"
+#include "force_slice.cuh"
 #include "force_x2.cuh"
 
 namespace nb {
@@ -77,6 +78,7 @@ int occupancy_instance(int *blocks)
 template <int MODE>
 cudaError_t force_dispatch(const ForceParams &P, const ForceConfig &cfg, cudaStream_t s)
 {
+    if (cfg.slice) return launch_force_slice<MODE>(P, cfg, s);
     if (cfg.jsub > 1) return launch_force_jsub<MODE>(P, cfg, s);
 #define NB_CASE(T, I) \
     if (cfg.threads == T && cfg.ipt == I) return launch_force_instance<MODE, T, I>(P, cfg, s);

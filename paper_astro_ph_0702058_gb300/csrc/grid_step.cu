@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) grid_step_kernel(const GrArgs A
     constexpr int PW = DSW ? 12 : 6;  // floats per partial
     extern __shared__ __align__(16) float jsm[];  // NA x SJ: x, y, z, m, vx, vy, vz (, x_lo, y_lo, z_lo)
     __shared__ float f_hi[kGrThreads][6], f_lo[kGrThreads][6];  // forces of up to kGrThreads own rows
-    __shared__ float wred[kGrWarps][6][2];
+    __shared__ float wred[kGrWarps][7][2];
     __shared__ unsigned long long red_u64[32];
     __shared__ int warp_tot[kGrWarps];
     __shared__ unsigned long long s_tb;

@@ -109,6 +109,7 @@ struct ForceConfig {
     int tiles_per_split;  // tiles of kJTile j in the longest range (lengths differ by at most one)
     int n_iblk;           // i-blocks (gridDim.x)
     int jsub = 1;         // threads per row, each taking 1/jsub of every tile (1 or 4)
+    int slice = 0;        // 1: the slice shape (one CTA per SM, split = CTAs; force_slice.cuh)
 };
 // The j-subgroup shape: 256 threads, 64 rows of 4 subgroups (packed plain and compensated modes).
 constexpr int kJSubThreads = 256;

@@ -54,6 +54,48 @@ def test_force_n65536_sweep_sampled(torch, mode, n_act):
         assert st["last_j_split"] > 1  # small blocks spread j over the GPU
 
 
+@pytest.mark.parametrize("mode", ["plain", "comp"])
+@pytest.mark.parametrize("n,n_act,eps2", [(65536, 512, EPS2), (65536, 777, EPS2), (65536, 4096, EPS2),
+                                          (65536, 8191, EPS2), (20001, 3000, EPS2), (16384, 1000, EPS2),
+                                          (20001, 600, 0.0)])
+def test_force_slice_shape(torch, mode, n, n_act, eps2):
+    """Mid-size blocks of streams of 64 tiles or more take the slice shape: one CTA of 512 threads per SM,
+    each over its slice of the stream (ragged at 20001, the last slices in the padding), j-split = SMs.
+    Up to 1000 rows against the FP64 oracle, potential included (eps = 0: the pair j = i masked)."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    m, x, v = plummer_sphere(n, 5)
+    act = active_subset(n, n_act, 13)
+    with _sim(m, x, v, eps2, mode) as sim:
+        sim.predict(0.0)
+        acc, jerk, pot = gpu_force(sim, act)
+        st = sim.stats()
+    assert st["last_threads"] == 512 and st["last_j_split"] == n_sm, st
+    rows = np.linspace(0, n_act - 1, min(n_act, 1000)).astype(int)
+    ra, rk, rp = oracle.force(m, x, v, eps2, act[rows])
+    assert np.all(np.isfinite(acc)) and np.all(np.isfinite(pot))
+    check_force(mode, m, x, v, eps2, act[rows], (acc[rows], jerk[rows], pot[rows]), (ra, rk, rp),
+                f"slice n={n} n_act={n_act} eps2={eps2}")
+
+
+def test_force_slice_rejects_bad_index(torch):
+    from paper_astro_ph_0702058_gb300 import NBodyError
+    n = 20001
+    m, x, v = plummer_sphere(n, 6)
+    act = active_subset(n, 700, 2).copy()
+    act[333] = n
+    with _sim(m, x, v, EPS2, "comp") as sim:
+        sim.predict(0.0)
+        with pytest.raises(NBodyError) as e:
+            gpu_force(sim, act)
+        assert e.value.code == -1
+        good = active_subset(n, 700, 3)
+        acc, jerk, pot = gpu_force(sim, good)
+        assert sim.stats()["last_threads"] == 512
+    rows = np.arange(0, 700, 7)
+    ra, rk, rp = oracle.force(m, x, v, EPS2, good[rows])
+    check_force("comp", m, x, v, EPS2, good[rows], (acc[rows], jerk[rows], pot[rows]), (ra, rk, rp), "after a bad index")
+
+
 def test_comp_more_accurate_than_plain(torch):
     """Compensated p99 error strictly below plain's at N = 65536 (acc, jerk, pot)."""
     n = 65536
