@@ -105,7 +105,11 @@ typedef struct {
     int j_sub;        /* force tuning, plain and compensated modes: 0 = automatic (4 for
                          blocks of 512 to 8191 rows when j_tile and i_block are 0, else 1);
                          1 = one thread per row; 4 = 256 threads as 64 rows x 4 threads,
-                         each taking a quarter of every j-tile (j_tile, i_block ignored)    */
+                         each taking a quarter of every j-tile (j_tile, i_block ignored).
+                         With all four force-tuning fields 0, blocks of 512 to 8191 rows of
+                         streams of 16384 to 3584 x SMs particles take the slice shape
+                         instead: one block of 512 threads per SM over its contiguous
+                         slice of the j-stream held in shared memory, j_split = SMs       */
     void *stream;     /* cudaStream_t for all work of the context, or NULL                  */
 } nbody_params;
 
