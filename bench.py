@@ -767,7 +767,8 @@ def ensemble_workload(args):
            "one_context_per_cluster": {"sample": len(sample), "s_per_cluster": per_cluster_s,
                                        "clusters_per_s": 1.0 / per_cluster_s,
                                        "pairs_per_s": single_pairs / single if sample else None,
-                                       "stepping": "nbody_step: device-side block loop in one CUDA graph",
+                                       "stepping": "nbody_step: the one-cluster block-step kernel (n_pad <= 4096), "
+                                                   "the whole-GPU block-step kernel above",
                                        "setup_s_per_cluster": setup / len(sample) if sample else None},
            "speedup_clusters_per_s": (n_cl / wall) * per_cluster_s,
            "energy_error_median": float(np.median(np.abs((ek + ep - e0) / e0))),
