@@ -31,3 +31,13 @@ def test_roofline_arithmetic():
     assert abs(r["achieved"] - n * (n - 1) / 1e9) < 0.01
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-4
     assert abs(r["frac_at_sampled_clock"] - 2 * r["frac"]) < 1e-3
+
+
+def test_traffic_record_matches_the_kernel_sources():
+    """The committed ncu DRAM-traffic record of the benchmarked launch is keyed on the force kernel's code;
+    it must match the sources as they stand, or the bench line reports no traffic."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for mode in ("plain", "comp"):
+        t = bench.measured_traffic(mode, 1 << 20, [256, 1, 2])
+        assert t is not None and t > 0, mode
