@@ -32,7 +32,9 @@
 // timeout flag; the cooperative launch guarantees that all CTAs are resident.
 // The loop stops, every CTA alike, at a block past t_end, a raised stop flag, a
 // spent budget or a block larger than rows_max; that block's list and size are
-// left for the host, which runs it through the separate kernels.
+// left for the host, and for a larger block also the j-stream predicted to its
+// time (each CTA its particles), so that the host runs it through the separate
+// force kernel and corrector alone.
 //
 // The forces of a block are the separate kernels' pair terms summed in another
 // order (per CTA, then across CTAs), so the state differs from theirs by
